@@ -1,0 +1,61 @@
+// Internal interface of the MTTKRP launcher (step a1).
+#pragma once
+
+#include "ntf_common.cuh"
+
+namespace ntf {
+
+// Tensor view shared by the MTTKRP, residual and norm kernels.
+struct TensorView {
+    int order = 0;
+    int64_t dims[NTF_MAX_ORDER] = {0};
+    ntf_dtype dtype = NTF_F32;
+    int64_t ld = 0;      // row pitch of the last mode, elements
+    int es = 4;          // element size, bytes
+    const void* data = nullptr;
+    int64_t C = 0, Ii = 0, n_o = 0;   // last dim, second-to-last dim, product of the others
+    int64_t rows() const { return Ii * n_o; }
+    int64_t numel() const { return rows() * C; }
+};
+
+// Validates an ntf_tensor and fills the view (NTF_EINVAL with a message on error).
+ntf_status make_view(const ntf_tensor* T, TensorView* v);
+
+enum class ModeKind { Inner, Outer, Last };
+
+struct MttkrpPlan {
+    ModeKind kind;
+    int mode, rank, RP, R, n_pb;
+    int I_T, O_T;
+    int64_t nb, n_ot, n_tiles;
+    int n_kc;
+    int G;               // streaming CTAs along the tile axis
+    int n_cb;            // last mode: 64-column blocks
+    int Smax;
+    int64_t Cpad;
+    // workspace layout (byte offsets)
+    size_t off_Fc, off_Fi, off_W, off_part, total;
+};
+
+ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* plan);
+
+// Cached 3-D tensor map of T for a plan's tile shape.
+struct TmapCache {
+    bool valid = false;
+    const void* data = nullptr;
+    int I_T = 0, O_T = 0;
+    CUtensorMap map;
+};
+
+// Optional CUDA-event timing of the streaming kernel.
+struct StreamTimer {
+    cudaEvent_t start = nullptr, stop = nullptr;
+};
+
+ntf_status run_mttkrp(const TensorView& v, const MttkrpPlan& plan, const float* const* factors, float* out,
+                      void* workspace, cudaStream_t st, TmapCache* cache, StreamTimer* timer);
+
+int num_sms();
+ntf_status configure_mttkrp(const TensorView& v, const MttkrpPlan& P);
+
+}  // namespace ntf

@@ -1,0 +1,449 @@
+// Host side of the MTTKRP (step a1): planning, workspace layout, the small
+// pack / weight-table / reduction kernels, and the launch sequence
+//   pack factors -> weight table W -> streaming kernel -> reduction.
+#include "mttkrp.cuh"
+#include "mttkrp_kernels.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+namespace ntf {
+
+// ---------------------------------------------------------------------------
+// tensor view
+// ---------------------------------------------------------------------------
+ntf_status make_view(const ntf_tensor* T, TensorView* v) {
+    if (!T) return fail(NTF_EINVAL, "tensor is NULL");
+    if (T->order < 2 || T->order > NTF_MAX_ORDER)
+        return fail(NTF_EINVAL, "tensor order must be in [2, 8], got " + std::to_string(T->order));
+    if (T->dtype != NTF_F32 && T->dtype != NTF_BF16) return fail(NTF_EINVAL, "unknown tensor dtype");
+    if (!T->data) return fail(NTF_EINVAL, "tensor data is NULL");
+    if (reinterpret_cast<uintptr_t>(T->data) % 16) return fail(NTF_EINVAL, "tensor data must be 16-byte aligned");
+    v->order = T->order;
+    for (int l = 0; l < T->order; ++l) {
+        if (T->dims[l] < 1) return fail(NTF_EINVAL, "tensor dims must be >= 1");
+        if (T->dims[l] > (int64_t(1) << 31)) return fail(NTF_EINVAL, "tensor dim exceeds 2^31");
+        v->dims[l] = T->dims[l];
+    }
+    v->dtype = T->dtype;
+    v->es = T->dtype == NTF_F32 ? 4 : 2;
+    v->C = T->dims[T->order - 1];
+    v->ld = T->ld ? T->ld : v->C;
+    if (v->ld < v->C) return fail(NTF_EINVAL, "tensor ld must be >= dims[order-1]");
+    if ((v->ld * v->es) % 16)
+        return fail(NTF_EINVAL, "tensor row pitch ld*sizeof(element) must be a multiple of 16 bytes (ld=" +
+                                    std::to_string(v->ld) + "); pad the last mode or use ntf_tensor_to_bf16/ntf_solve");
+    v->Ii = T->dims[T->order - 2];
+    v->n_o = 1;
+    for (int l = 0; l < T->order - 2; ++l) v->n_o *= T->dims[l];
+    v->data = T->data;
+    return NTF_OK;
+}
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
+// ---------------------------------------------------------------------------
+// tensor map
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+ntf_status encode_tensor_map_3d(CUtensorMap* map, ntf_dtype dtype, const void* base, uint64_t d0, uint64_t d1,
+                                uint64_t d2, uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t box0,
+                                uint32_t box1, uint32_t box2) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return fail(NTF_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {stride1_bytes, stride2_bytes};
+    const cuuint32_t box[3] = {box0, box1, box2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, dtype == NTF_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(NTF_ECUDA, "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+    return NTF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------
+static double util(int64_t n, int64_t t) { return (double)n / (double)(t * ceil_div(n, t)); }
+
+// tile shape (I_T inner x O_T outer, I_T * O_T = 128) with the fewest padded rows
+static void choose_tile(int64_t Ii, int64_t n_o, int max_IT, int* I_T, int* O_T) {
+    double best = -1;
+    for (int it = max_IT; it >= 1; it >>= 1) {
+        const int ot = 128 / it;
+        const double u = util(Ii, it) * util(n_o, ot);
+        if (u > best + 1e-9) { best = u; *I_T = it; *O_T = ot; }
+    }
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
+    if (rank < 1 || rank > NTF_MAX_RANK) return fail(NTF_EINVAL, "rank must be in [1, 64]");
+    if (mode < 0 || mode >= v.order) return fail(NTF_EINVAL, "mode out of range");
+    MttkrpPlan P{};
+    P.mode = mode;
+    P.rank = rank;
+    if (rank <= 32) {
+        P.RP = (int)round_up(rank, 4);
+        if (P.RP == 28) P.RP = 32;    // kernels are instantiated for 4..24 and 32 columns
+        P.R = P.RP;
+    } else {
+        P.RP = 64;
+        P.R = 32;
+    }
+    P.n_pb = P.RP / P.R;
+    P.kind = mode == v.order - 1 ? ModeKind::Last : mode == v.order - 2 ? ModeKind::Inner : ModeKind::Outer;
+    if (P.kind == ModeKind::Inner) choose_tile(v.Ii, v.n_o, 32, &P.I_T, &P.O_T);
+    else if (P.kind == ModeKind::Outer) { P.I_T = 128; P.O_T = 1; }
+    else choose_tile(v.Ii, v.n_o, 128, &P.I_T, &P.O_T);
+    P.nb = ceil_div(v.Ii, P.I_T);
+    P.n_ot = ceil_div(v.n_o, P.O_T);
+    P.n_tiles = P.nb * P.n_ot;
+    P.n_kc = (int)ceil_div(v.C, kStageCols);
+    const int sms = num_sms();
+    P.n_cb = (int)ceil_div(v.C, kStageCols);
+    P.Cpad = (int64_t)P.n_cb * kStageCols;
+    if (P.kind == ModeKind::Last) {
+        int gs = sms / P.n_cb;
+        if (gs < 1) gs = 1;
+        if (gs > P.n_tiles) gs = (int)P.n_tiles;
+        P.G = gs;
+    } else {
+        P.G = (int)std::min<int64_t>(P.n_tiles, sms);
+    }
+    P.Smax = 1;
+    if (P.kind == ModeKind::Inner) {
+        for (int g = 0; g < P.G; ++g) {
+            const int64_t b = (P.n_tiles * g) / P.G, e = (P.n_tiles * (g + 1)) / P.G;
+            if (e > b) {
+                const int s = (int)((e - 1) / P.n_ot - b / P.n_ot + 1);
+                if (s > P.Smax) P.Smax = s;
+            }
+        }
+    }
+    size_t off = 0;
+    P.off_Fc = off;
+    off = align256(off + sizeof(float) * (size_t)round_up(v.C, kStageCols) * P.RP);
+    P.off_Fi = off;
+    off = align256(off + sizeof(float) * (size_t)v.Ii * P.RP);
+    P.off_W = off;
+    off = align256(off + sizeof(float) * (size_t)v.n_o * P.RP);
+    P.off_part = off;
+    size_t part = 0;
+    if (P.kind == ModeKind::Inner)
+        part = (size_t)P.G * P.Smax * kStreamWarps * P.I_T * P.RP;
+    else if (P.kind == ModeKind::Outer)
+        part = (size_t)v.n_o * P.nb * kStreamWarps * P.RP;
+    else
+        part = (size_t)P.G * P.Cpad * P.RP;
+    off = align256(off + sizeof(float) * part);
+    P.total = off;
+    *p = P;
+    return NTF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+struct FactorPtrs {
+    const float* a[NTF_MAX_ORDER];
+};
+struct Dims {
+    int64_t d[NTF_MAX_ORDER];
+};
+
+// out (rows_out x RP) <- A (rows x r) with zero padding
+__global__ void k_pack(const float* __restrict__ A, int64_t rows, int r, int RP, int64_t rows_out,
+                       float* __restrict__ out) {
+    const int64_t n = rows_out * RP;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / RP;
+        const int p = (int)(idx % RP);
+        out[idx] = (i < rows && p < r) ? A[i * r + p] : 0.f;
+    }
+}
+
+// W(o,p) = prod_{l < N-2, l != skip} A_l(i_l(o), p)   (o in C order over modes 0..N-3)
+__global__ void k_weights(FactorPtrs F, Dims D, int order, int skip, int r, int RP, int64_t n_o,
+                          float* __restrict__ W) {
+    const int64_t n = n_o * RP;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = idx / RP;
+        const int p = (int)(idx % RP);
+        float w = 0.f;
+        if (p < r) {
+            w = 1.f;
+            int64_t rem = o;
+            for (int l = order - 3; l >= 0; --l) {
+                const int64_t il = rem % D.d[l];
+                rem /= D.d[l];
+                if (l != skip) w *= F.a[l][il * r + p];
+            }
+        }
+        W[idx] = w;
+    }
+}
+
+struct ReduceParams {
+    int64_t n_tiles, n_ot, nb, Ii, n_o, C, Cpad;
+    int G, Smax, I_T, RP, r;
+    // outer mode
+    int64_t In, stride, hi_count;
+    const float* part;
+    const float* W;
+    float* out;
+};
+
+__global__ void k_reduce_inner(const ReduceParams P) {
+    const int64_t n = P.Ii * P.r;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / P.r;
+        const int p = (int)(idx % P.r);
+        const int64_t ib = i / P.I_T;
+        const int b = (int)(i % P.I_T);
+        float s = 0.f;
+        for (int g = 0; g < P.G; ++g) {
+            const int64_t tb = (P.n_tiles * g) / P.G, te = (P.n_tiles * (g + 1)) / P.G;
+            if (te <= tb) continue;
+            const int64_t first = tb / P.n_ot, last = (te - 1) / P.n_ot;
+            if (ib < first || ib > last) continue;
+            const int seg = (int)(ib - first);
+            for (int w = 0; w < kStreamWarps; ++w)
+                s += P.part[((((int64_t)g * P.Smax + seg) * kStreamWarps + w) * P.I_T + b) * P.RP + p];
+        }
+        P.out[idx] = s;
+    }
+}
+
+__global__ void k_reduce_outer(const ReduceParams P) {
+    const int64_t n = P.In * P.r;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = idx / P.r;
+        const int p = (int)(idx % P.r);
+        float s = 0.f;
+        for (int64_t hi = 0; hi < P.hi_count; ++hi)
+            for (int64_t lo = 0; lo < P.stride; ++lo) {
+                const int64_t o = (hi * P.In + j) * P.stride + lo;
+                float so = 0.f;
+                for (int64_t ib = 0; ib < P.nb; ++ib)
+                    for (int w = 0; w < kStreamWarps; ++w)
+                        so += P.part[((o * P.nb + ib) * kStreamWarps + w) * P.RP + p];
+                s = fmaf(P.W[o * P.RP + p], so, s);
+            }
+        P.out[idx] = s;
+    }
+}
+
+__global__ void k_reduce_last(const ReduceParams P) {
+    const int64_t n = P.C * P.r;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = idx / P.r;
+        const int p = (int)(idx % P.r);
+        float s = 0.f;
+        for (int g = 0; g < P.G; ++g) s += P.part[((int64_t)g * P.Cpad + c) * P.RP + p];
+        P.out[idx] = s;
+    }
+}
+
+static int grid_for(int64_t n, int threads) {
+    int64_t b = ceil_div(n, threads);
+    if (b > 4096) b = 4096;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// launch sequence
+// ---------------------------------------------------------------------------
+ntf_status run_mttkrp(const TensorView& v, const MttkrpPlan& P, const float* const* factors, float* out,
+                      void* workspace, cudaStream_t st, TmapCache* cache, StreamTimer* timer) {
+    const int N = v.order, r = P.rank, n = P.mode;
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    float* Fc = reinterpret_cast<float*>(ws + P.off_Fc);
+    float* Fi = reinterpret_cast<float*>(ws + P.off_Fi);
+    float* W = reinterpret_cast<float*>(ws + P.off_W);
+    float* part = reinterpret_cast<float*>(ws + P.off_part);
+
+    // tensor map
+    CUtensorMap local_map;
+    const CUtensorMap* map = &local_map;
+    if (cache && cache->valid && cache->data == v.data && cache->I_T == P.I_T && cache->O_T == P.O_T) {
+        map = &cache->map;
+    } else {
+        const uint32_t box0 = 128 / v.es;
+        ntf_status s = encode_tensor_map_3d(&local_map, v.dtype, v.data, (uint64_t)v.C, (uint64_t)v.Ii,
+                                            (uint64_t)v.n_o, (uint64_t)(v.ld * v.es),
+                                            (uint64_t)(v.Ii * v.ld * v.es), box0, (uint32_t)P.I_T, (uint32_t)P.O_T);
+        if (s != NTF_OK) return s;
+        if (cache) {
+            cache->valid = true;
+            cache->data = v.data;
+            cache->I_T = P.I_T;
+            cache->O_T = P.O_T;
+            cache->map = local_map;
+            map = &cache->map;
+        }
+    }
+
+    // 1. packed factors and weight table
+    if (P.kind != ModeKind::Last) {
+        const int64_t rows_out = round_up(v.C, kStageCols);
+        k_pack<<<grid_for(rows_out * P.RP, 256), 256, 0, st>>>(factors[N - 1], v.C, r, P.RP, rows_out, Fc);
+        NTF_LAUNCH_CHECK("k_pack(A_last)");
+    }
+    if (P.kind != ModeKind::Inner) {
+        k_pack<<<grid_for(v.Ii * P.RP, 256), 256, 0, st>>>(factors[N - 2], v.Ii, r, P.RP, v.Ii, Fi);
+        NTF_LAUNCH_CHECK("k_pack(A_second_to_last)");
+    }
+    {
+        FactorPtrs F{};
+        Dims D{};
+        for (int l = 0; l < N; ++l) {
+            F.a[l] = factors[l];
+            D.d[l] = v.dims[l];
+        }
+        const int skip = P.kind == ModeKind::Outer ? n : -1;
+        k_weights<<<grid_for(v.n_o * P.RP, 256), 256, 0, st>>>(F, D, N, skip, r, P.RP, v.n_o, W);
+        NTF_LAUNCH_CHECK("k_weights");
+    }
+
+    // 2. streaming kernel
+    StreamParams S{};
+    S.C = v.C;
+    S.Ii = v.Ii;
+    S.n_o = v.n_o;
+    S.I_T = P.I_T;
+    S.O_T = P.O_T;
+    S.nb = P.nb;
+    S.n_ot = P.n_ot;
+    S.n_tiles = P.n_tiles;
+    S.n_kc = P.n_kc;
+    S.RP = P.RP;
+    S.Smax = P.Smax;
+    S.Cpad = P.Cpad;
+    S.Fc = Fc;
+    S.Fi = Fi;
+    S.W = W;
+    S.part = part;
+    S.err = device_error_word();
+    const int kind = P.kind == ModeKind::Inner ? 0 : P.kind == ModeKind::Outer ? 1 : 2;
+    dim3 grid;
+    size_t smem;
+    if (P.kind == ModeKind::Last) {
+        grid = dim3(P.G, P.n_cb, P.n_pb);
+        smem = stream_last_smem(v.es, P.R);
+    } else {
+        grid = dim3(P.G, P.n_pb, 1);
+        smem = stream_rows_smem(v.es, P.RP);
+    }
+    if (timer && timer->start) NTF_CUDA_TRY(cudaEventRecord(timer->start, st));
+    cudaError_t e = v.dtype == NTF_F32 ? launch_stream_f32(kind, P.R, grid, smem, st, *map, S)
+                                       : launch_stream_bf16(kind, P.R, grid, smem, st, *map, S);
+    count_launch();
+    if (e != cudaSuccess) return cuda_fail(e, "MTTKRP streaming kernel launch");
+    if (timer && timer->stop) NTF_CUDA_TRY(cudaEventRecord(timer->stop, st));
+
+    // 3. deterministic reduction into the user's I_n x r output
+    ReduceParams R{};
+    R.n_tiles = P.n_tiles;
+    R.n_ot = P.n_ot;
+    R.nb = P.nb;
+    R.Ii = v.Ii;
+    R.n_o = v.n_o;
+    R.C = v.C;
+    R.Cpad = P.Cpad;
+    R.G = P.G;
+    R.Smax = P.Smax;
+    R.I_T = P.I_T;
+    R.RP = P.RP;
+    R.r = r;
+    R.part = part;
+    R.W = W;
+    R.out = out;
+    if (P.kind == ModeKind::Inner) {
+        k_reduce_inner<<<grid_for(v.Ii * r, 128), 128, 0, st>>>(R);
+        NTF_LAUNCH_CHECK("k_reduce_inner");
+    } else if (P.kind == ModeKind::Outer) {
+        R.In = v.dims[n];
+        int64_t stride = 1;
+        for (int l = n + 1; l < N - 2; ++l) stride *= v.dims[l];
+        R.stride = stride;
+        R.hi_count = v.n_o / (R.In * stride);
+        k_reduce_outer<<<grid_for(R.In * r, 128), 128, 0, st>>>(R);
+        NTF_LAUNCH_CHECK("k_reduce_outer");
+    } else {
+        k_reduce_last<<<grid_for(v.C * r, 128), 128, 0, st>>>(R);
+        NTF_LAUNCH_CHECK("k_reduce_last");
+    }
+    return NTF_OK;
+}
+
+}  // namespace ntf
+
+namespace ntf {
+cudaError_t launch_weights_all(const TensorView& v, const float* const* factors, int r, int RP, float* W,
+                               cudaStream_t st) {
+    FactorPtrs F{};
+    Dims D{};
+    for (int l = 0; l < v.order; ++l) {
+        F.a[l] = factors[l];
+        D.d[l] = v.dims[l];
+    }
+    k_weights<<<grid_for(v.n_o * RP, 256), 256, 0, st>>>(F, D, v.order, -1, r, RP, v.n_o, W);
+    count_launch();
+    return cudaGetLastError();
+}
+}  // namespace ntf
+
+namespace ntf {
+// Opt the streaming kernel of a plan in to its shared-memory size without
+// launching it (so that no attribute call happens inside a graph capture).
+ntf_status configure_mttkrp(const TensorView& v, const MttkrpPlan& P) {
+    const int kind = P.kind == ModeKind::Inner ? 0 : P.kind == ModeKind::Outer ? 1 : 2;
+    const size_t smem = P.kind == ModeKind::Last ? stream_last_smem(v.es, P.R) : stream_rows_smem(v.es, P.RP);
+    CUtensorMap dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    StreamParams S{};
+    cudaError_t e = v.dtype == NTF_F32 ? launch_stream_f32(kind, P.R, dim3(0, 1, 1), smem, nullptr, dummy, S)
+                                       : launch_stream_bf16(kind, P.R, dim3(0, 1, 1), smem, nullptr, dummy, S);
+    if (e != cudaSuccess) return cuda_fail(e, "configure MTTKRP kernel");
+    return NTF_OK;
+}
+}  // namespace ntf

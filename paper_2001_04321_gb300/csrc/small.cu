@@ -1,0 +1,649 @@
+// Kernels of steps a2-a8 other than the MTTKRP stream: Grams and their
+// Hadamard product (a2), HALS / projected-gradient block updates (a3), the HER
+// extrapolation (a4), the objective by reuse (a5), the restart decision (a6),
+// the explicit residual (a7), the bf16 cast (a8) and ||T||^2.
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, so every per-element
+// product here is FP32; FP64 only combines short FP32 partial sums and holds
+// the r x r Grams, the objective terms and the HER scalars.
+#include "small.cuh"
+
+#include <cmath>
+
+namespace ntf {
+
+// ---------------------------------------------------------------------------
+// block reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// sum over the block (blockDim multiple of 32, <= 1024); result valid in every thread
+__device__ double block_sum_d(double v, double* sbuf /* >= 33 doubles */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) sbuf[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double t = lane < nw ? sbuf[lane] : 0.0;
+        t = warp_sum_d(t);
+        if (lane == 0) sbuf[32] = t;
+    }
+    __syncthreads();
+    return sbuf[32];
+}
+
+// ---------------------------------------------------------------------------
+// a2: Gram A^T A (one CTA; FP32 over 32-row blocks, FP64 across blocks)
+// ---------------------------------------------------------------------------
+constexpr int kGramThreads = 512;
+constexpr int kGramChunk = 128;   // rows staged in shared memory at a time
+
+// Accumulates the upper triangle of A^T A into acc[] (pairs t, t+512, ...);
+// sA has room for kGramChunk * r floats.
+__device__ void gram_accumulate(const float* __restrict__ A, int64_t rows, int r, float* sA, double acc[5]) {
+    const int npairs = r * (r + 1) / 2;
+    for (int64_t r0 = 0; r0 < rows; r0 += kGramChunk) {
+        const int nrow = (int)(rows - r0 < kGramChunk ? rows - r0 : kGramChunk);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nrow * r; idx += blockDim.x) sA[idx] = A[r0 * r + idx];
+        __syncthreads();
+        int k = 0;
+        for (int q = threadIdx.x; q < npairs; q += blockDim.x, ++k) {
+            // pair index -> (p, c) with p <= c
+            int p = 0, rem = q;
+            while (rem >= r - p) { rem -= r - p; ++p; }
+            const int c = p + rem;
+            for (int b0 = 0; b0 < nrow; b0 += 32) {
+                const int b1 = min(nrow, b0 + 32);
+                float s = 0.f;
+                for (int i = b0; i < b1; ++i) s = fmaf(sA[i * r + p], sA[i * r + c], s);
+                acc[k] += (double)s;
+            }
+        }
+    }
+}
+
+__device__ void gram_store(int r, const double acc[5], double* G) {
+    const int npairs = r * (r + 1) / 2;
+    int k = 0;
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x, ++k) {
+        int p = 0, rem = q;
+        while (rem >= r - p) { rem -= r - p; ++p; }
+        const int c = p + rem;
+        G[p * r + c] = acc[k];
+        G[c * r + p] = acc[k];
+    }
+}
+
+__global__ void __launch_bounds__(kGramThreads) k_gram(const float* __restrict__ A, int64_t rows, int r,
+                                                       double* __restrict__ G) {
+    extern __shared__ float sA[];
+    double acc[5] = {0, 0, 0, 0, 0};
+    gram_accumulate(A, rows, r, sA, acc);
+    gram_store(r, acc, G);
+}
+
+size_t gram_smem(int r) { return sizeof(float) * kGramChunk * r; }
+
+cudaError_t launch_gram(const float* A, int64_t rows, int r, double* G, cudaStream_t st) {
+    k_gram<<<1, kGramThreads, gram_smem(r), st>>>(A, rows, r, G);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// V = Hadamard product of grams[l], l != skip
+__global__ void k_hadamard(GramPtrs P, int order, int skip, int r, double* __restrict__ V) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < r * r; q += gridDim.x * blockDim.x) {
+        double v = 1.0;
+        for (int l = 0; l < order; ++l)
+            if (l != skip) v *= P.g[l][q];
+        V[q] = v;
+    }
+}
+
+cudaError_t launch_hadamard(const GramPtrs& P, int order, int skip, int r, double* V, cudaStream_t st) {
+    k_hadamard<<<(r * r + 255) / 256, 256, 0, st>>>(P, order, skip, r, V);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a3: block updates.  One thread owns one row of A (rows are independent in
+// both HALS and PGD); R >= r is the register width.
+// ---------------------------------------------------------------------------
+constexpr int kBcdThreads = 512;
+
+template <int R>
+__device__ __forceinline__ void load_row(const float* __restrict__ src, int64_t i, int r, float (&v)[R]) {
+#pragma unroll
+    for (int p = 0; p < R; ++p) v[p] = p < r ? src[i * r + p] : 0.f;
+}
+
+// One HALS sweep (Sec. 2.1.4) of row a against m with V in shared memory
+// (Vs row-major R x R, zero padded).  Returns sum of squared changes.
+template <int R>
+__device__ __forceinline__ float hals_row(float (&a)[R], const float (&m)[R], const float* Vs, int r) {
+    float d2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        if (j < r) {
+            const float vjj = Vs[j * R + j];
+            if (vjj > 0.f) {
+                // num = M(i,j) - sum_{l != j} a_l V(l,j), in four independent partial sums
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+                for (int l = 0; l < R; l += 4) {
+                    s0 = fmaf(l + 0 == j ? 0.f : a[l + 0], Vs[(l + 0) * R + j], s0);
+                    if (l + 1 < R) s1 = fmaf(l + 1 == j ? 0.f : a[l + 1], Vs[(l + 1) * R + j], s1);
+                    if (l + 2 < R) s2 = fmaf(l + 2 == j ? 0.f : a[l + 2], Vs[(l + 2) * R + j], s2);
+                    if (l + 3 < R) s3 = fmaf(l + 3 == j ? 0.f : a[l + 3], Vs[(l + 3) * R + j], s3);
+                }
+                const float num = m[j] - ((s0 + s1) + (s2 + s3));
+                const float nv = fmaxf(num, 0.f) / vjj;
+                const float d = nv - a[j];
+                d2 = fmaf(d, d, d2);
+                a[j] = nv;
+            }
+        }
+    }
+    return d2;
+}
+
+// One projected-gradient step (Sec. 2.2): a <- max(0, a - (a V - m)/L)
+template <int R>
+__device__ __forceinline__ float pgd_row(float (&a)[R], const float (&m)[R], const float* Vs, int r, float invL) {
+    float na[R];
+    float d2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        float g = -m[j];
+#pragma unroll
+        for (int l = 0; l < R; ++l) g = fmaf(a[l], Vs[l * R + j], g);
+        const float v = fmaxf(fmaf(-g, invL, a[j]), 0.f);
+        na[j] = j < r ? v : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const float d = na[j] - a[j];
+        d2 = fmaf(d, d, d2);
+        a[j] = na[j];
+    }
+    return d2;
+}
+
+template <int R>
+__device__ void stage_V(const double* __restrict__ V, int r, float* Vs) {
+    for (int q = threadIdx.x; q < R * R; q += blockDim.x) {
+        const int l = q / R, j = q % R;
+        Vs[q] = (l < r && j < r) ? (float)V[l * r + j] : 0.f;
+    }
+}
+
+// Whole inner loop in one CTA (rows <= kBcdThreads).  method 0 = HALS, 1 = PGD.
+template <int R>
+__global__ void __launch_bounds__(kBcdThreads) k_bcd_local(int method, float* __restrict__ A, int64_t rows, int r,
+                                                           const float* __restrict__ M, const double* __restrict__ V,
+                                                           const double* __restrict__ Lptr, int inner_max,
+                                                           double tol2, int* __restrict__ sweeps_out) {
+    __shared__ float Vs[R * R];
+    __shared__ double sbuf[33];
+    stage_V<R>(V, r, Vs);
+    __syncthreads();
+    const int64_t i = threadIdx.x;
+    const bool live = i < rows;
+    float a[R], m[R];
+    if (live) {
+        load_row<R>(A, i, r, a);
+        load_row<R>(M, i, r, m);
+    } else {
+#pragma unroll
+        for (int p = 0; p < R; ++p) a[p] = m[p] = 0.f;
+    }
+    const float invL = (method == 1 && Lptr && *Lptr > 0.0) ? (float)(1.0 / *Lptr) : 0.f;
+    double delta1 = 0.0;
+    int s = 0;
+    for (;;) {
+        ++s;
+        float d2 = 0.f;
+        if (live) d2 = method == 0 ? hals_row<R>(a, m, Vs, r) : pgd_row<R>(a, m, Vs, r, invL);
+        const double tot = block_sum_d((double)d2, sbuf);
+        if (s == 1) delta1 = tot;
+        if (s >= inner_max || tot <= tol2 * delta1) break;
+    }
+    if (live)
+#pragma unroll
+        for (int p = 0; p < R; ++p)
+            if (p < r) A[i * r + p] = a[p];
+    if (threadIdx.x == 0 && sweeps_out) *sweeps_out = s;
+}
+
+// One sweep/step across many CTAs.  Sweep s (1-based) first decides, from the
+// partial sums of sweeps 1 and s-1, whether the inner loop has stopped.
+// parts: [2][gridDim] doubles (by sweep parity) + [gridDim] for sweep 1; flag: stopped.
+template <int R>
+__global__ void __launch_bounds__(kBcdThreads) k_bcd_sweep(int method, float* __restrict__ A, int64_t rows, int r,
+                                                           const float* __restrict__ M, const double* __restrict__ V,
+                                                           const double* __restrict__ Lptr, int s, double tol2,
+                                                           double* __restrict__ parts, int* __restrict__ stopped) {
+    __shared__ float Vs[R * R];
+    __shared__ double sbuf[33];
+    __shared__ int stop_sh;
+    const int G = gridDim.x;
+    if (threadIdx.x == 0) {
+        int stop = (s == 1) ? 0 : *stopped;
+        if (s > 1 && !stop) {
+            double d1 = 0.0, dp = 0.0;
+            for (int g = 0; g < G; ++g) {
+                d1 += parts[2 * G + g];
+                dp += parts[((s - 1) & 1) * G + g];
+            }
+            if (dp <= tol2 * d1) stop = 1;
+        }
+        stop_sh = stop;
+    }
+    stage_V<R>(V, r, Vs);
+    __syncthreads();
+    if (stop_sh) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *stopped = 1;
+        return;
+    }
+    if (s == 1 && blockIdx.x == 0 && threadIdx.x == 0) *stopped = 0;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float d2 = 0.f;
+    if (i < rows) {
+        float a[R], m[R];
+        load_row<R>(A, i, r, a);
+        load_row<R>(M, i, r, m);
+        const float invL = (method == 1 && Lptr && *Lptr > 0.0) ? (float)(1.0 / *Lptr) : 0.f;
+        d2 = method == 0 ? hals_row<R>(a, m, Vs, r) : pgd_row<R>(a, m, Vs, r, invL);
+#pragma unroll
+        for (int p = 0; p < R; ++p)
+            if (p < r) A[i * r + p] = a[p];
+    }
+    const double tot = block_sum_d((double)d2, sbuf);
+    if (threadIdx.x == 0) {
+        parts[(s & 1) * G + blockIdx.x] = tot;
+        if (s == 1) parts[2 * G + blockIdx.x] = tot;
+    }
+}
+
+// L = lambda_max(V) of the symmetric nonnegative r x r matrix V: FP32 power
+// iteration to a relative change below 1e-7 (at most 500 steps), then one
+// FP64 Rayleigh quotient.  One warp.
+__global__ void k_lambda_max(const double* __restrict__ V, int r, double* __restrict__ L) {
+    __shared__ float Vs[NTF_MAX_RANK * NTF_MAX_RANK];
+    __shared__ float x[NTF_MAX_RANK];
+    const int lane = threadIdx.x;
+    for (int q = lane; q < r * r; q += 32) Vs[q] = (float)V[q];
+    for (int j = lane; j < r; j += 32) x[j] = 1.f + 0.01f * j;
+    __syncwarp();
+    float lam = 0.f;
+    for (int it = 0; it < 500; ++it) {
+        float y0 = 0.f, y1 = 0.f;
+        if (lane < r)
+            for (int l = 0; l < r; ++l) y0 = fmaf(Vs[lane * r + l], x[l], y0);
+        if (lane + 32 < r)
+            for (int l = 0; l < r; ++l) y1 = fmaf(Vs[(lane + 32) * r + l], x[l], y1);
+        float nrm = y0 * y0 + y1 * y1;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+        nrm = sqrtf(nrm);
+        __syncwarp();
+        if (nrm > 0.f) {
+            if (lane < r) x[lane] = y0 / nrm;
+            if (lane + 32 < r) x[lane + 32] = y1 / nrm;
+        }
+        __syncwarp();
+        const bool done = fabsf(nrm - lam) <= 1e-7f * nrm;
+        lam = nrm;
+        if (done || nrm == 0.f) break;
+    }
+    // Rayleigh quotient x^T V x / x^T x in FP64
+    double num = 0.0, den = 0.0;
+    for (int j = lane; j < r; j += 32) {
+        double y = 0.0;
+        for (int l = 0; l < r; ++l) y += V[j * r + l] * (double)x[l];
+        num += (double)x[j] * y;
+        den += (double)x[j] * (double)x[j];
+    }
+    num = warp_sum_d(num);
+    den = warp_sum_d(den);
+    if (lane == 0) *L = den > 0.0 ? num / den : 0.0;
+}
+
+template <int R>
+static cudaError_t bcd_impl(int method, float* A, int64_t rows, int r, const float* M, const double* V,
+                            int inner_max, double tol, double* L, double* parts, int* stopped, cudaStream_t st) {
+    if (method == 1) {
+        k_lambda_max<<<1, 32, 0, st>>>(V, r, L);
+        count_launch();
+    }
+    const double tol2 = tol * tol;
+    if (rows <= kBcdThreads) {
+        k_bcd_local<R><<<1, kBcdThreads, 0, st>>>(method, A, rows, r, M, V, L, inner_max, tol2, nullptr);
+        count_launch();
+        return cudaGetLastError();
+    }
+    const int G = (int)((rows + kBcdThreads - 1) / kBcdThreads);
+    for (int s = 1; s <= inner_max; ++s) {
+        k_bcd_sweep<R><<<G, kBcdThreads, 0, st>>>(method, A, rows, r, M, V, L, s, tol2, parts, stopped);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+size_t bcd_workspace(int64_t rows) {
+    const int64_t G = (rows + kBcdThreads - 1) / kBcdThreads;
+    return 256 + sizeof(double) * (size_t)(3 * G + 8);
+}
+
+cudaError_t launch_bcd(int method, float* A, int64_t rows, int r, const float* M, const double* V, int inner_max,
+                       double tol, void* ws, cudaStream_t st) {
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    double* L = reinterpret_cast<double*>(w);
+    int* stopped = reinterpret_cast<int*>(w + 8);
+    double* parts = reinterpret_cast<double*>(w + 256);
+    const int R = r <= 4 ? 4 : r <= 8 ? 8 : r <= 12 ? 12 : r <= 16 ? 16 : r <= 20 ? 20 : r <= 24 ? 24 : r <= 32 ? 32 : 64;
+    switch (R) {
+        case 4: return bcd_impl<4>(method, A, rows, r, M, V, inner_max, tol, L, parts, stopped, st);
+        case 8: return bcd_impl<8>(method, A, rows, r, M, V, inner_max, tol, L, parts, stopped, st);
+        case 12: return bcd_impl<12>(method, A, rows, r, M, V, inner_max, tol, L, parts, stopped, st);
+        case 16: return bcd_impl<16>(method, A, rows, r, M, V, inner_max, tol, L, parts, stopped, st);
+        case 20: return bcd_impl<20>(method, A, rows, r, M, V, inner_max, tol, L, parts, stopped, st);
+        case 24: return bcd_impl<24>(method, A, rows, r, M, V, inner_max, tol, L, parts, stopped, st);
+        case 32: return bcd_impl<32>(method, A, rows, r, M, V, inner_max, tol, L, parts, stopped, st);
+        default: return bcd_impl<64>(method, A, rows, r, M, V, inner_max, tol, L, parts, stopped, st);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a4: extrapolation  A_hat = max(0, A + beta (A - A_prev))
+// ---------------------------------------------------------------------------
+__global__ void k_extrapolate(const float* __restrict__ A, const float* __restrict__ Ap,
+                              const double* __restrict__ beta, int64_t n, float* __restrict__ Ah) {
+    const float b = (float)*beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float a = A[i];
+        Ah[i] = fmaxf(fmaf(b, a - Ap[i], a), 0.f);
+    }
+}
+
+cudaError_t launch_extrapolate(const float* A, const float* Ap, const double* beta, int64_t n, float* Ah,
+                               cudaStream_t st) {
+    int64_t g = (n + 255) / 256;
+    if (g > 1024) g = 1024;
+    if (g < 1) g = 1;
+    k_extrapolate<<<(int)g, 256, 0, st>>>(A, Ap, beta, n, Ah);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a5: objective by reuse:  ||T||^2 - 2 <M, A> + sum(V (*) A^T A)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kGramThreads) k_objective(const double* __restrict__ tn, const float* __restrict__ M,
+                                                            const float* __restrict__ A, int64_t rows, int r,
+                                                            const double* __restrict__ V, double* __restrict__ out,
+                                                            double* __restrict__ G_out) {
+    extern __shared__ __align__(16) unsigned char obj_smem[];
+    __shared__ double sbuf[33];
+    double* Gs = reinterpret_cast<double*>(obj_smem);                    // r x r
+    float* sA = reinterpret_cast<float*>(obj_smem + sizeof(double) * r * r);  // kGramChunk x r
+    // <M, A>: FP32 products summed over at most 32 entries, then FP64
+    const int64_t n = rows * r;
+    double inner = 0.0;
+    for (int64_t b = (int64_t)threadIdx.x * 32; b < n; b += (int64_t)blockDim.x * 32) {
+        float s = 0.f;
+        const int64_t e = (n < b + 32) ? n : b + 32;
+        for (int64_t i = b; i < e; ++i) s = fmaf(M[i], A[i], s);
+        inner += (double)s;
+    }
+    inner = block_sum_d(inner, sbuf);
+    double acc[5] = {0, 0, 0, 0, 0};
+    gram_accumulate(A, rows, r, sA, acc);
+    __syncthreads();
+    gram_store(r, acc, Gs);
+    __syncthreads();
+    double quad = 0.0;
+    for (int q = threadIdx.x; q < r * r; q += blockDim.x) quad += V[q] * Gs[q];
+    quad = block_sum_d(quad, sbuf);
+    if (threadIdx.x == 0) *out = *tn - 2.0 * inner + quad;
+    if (G_out)
+        for (int q = threadIdx.x; q < r * r; q += blockDim.x) G_out[q] = Gs[q];
+}
+
+cudaError_t launch_objective(const double* tn, const float* M, const float* A, int64_t rows, int r, const double* V,
+                             double* out, double* G_out, cudaStream_t st) {
+    const size_t smem = sizeof(double) * r * r + gram_smem(r);
+    static size_t set_bytes = 0;
+    if (set_bytes < smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_objective, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_bytes = smem;
+    }
+    if (!M) return cudaSuccess;   // configuration only
+    k_objective<<<1, kGramThreads, smem, st>>>(tn, M, A, rows, r, V, out, G_out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// ||T||^2 and the explicit residual ||T - X||^2 (multi-CTA partials + final sum)
+// ---------------------------------------------------------------------------
+constexpr int kStreamRedThreads = 256;
+
+template <typename TE>
+__device__ __forceinline__ float load_elem(const TE* p);
+template <>
+__device__ __forceinline__ float load_elem<float>(const float* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float load_elem<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+template <typename TE>
+__global__ void __launch_bounds__(kStreamRedThreads) k_norm_sq(const TE* __restrict__ T, int64_t rows, int64_t C,
+                                                               int64_t ld, double* __restrict__ parts) {
+    __shared__ double sbuf[33];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double acc = 0.0;
+    for (int64_t row = warp_g; row < rows; row += nwarps) {
+        const TE* rp = T + row * ld;
+        float s = 0.f;
+        int cnt = 0;
+        for (int64_t c = lane; c < C; c += 32) {
+            const float v = load_elem<TE>(rp + c);
+            s = fmaf(v, v, s);
+            if (++cnt == 64) { acc += (double)s; s = 0.f; cnt = 0; }
+        }
+        acc += (double)s;
+    }
+    const double tot = block_sum_d(acc, sbuf);
+    if (threadIdx.x == 0) parts[blockIdx.x] = tot;
+}
+
+__global__ void k_sum_parts(const double* __restrict__ parts, int n, double* __restrict__ out) {
+    __shared__ double sbuf[33];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += parts[i];
+    acc = block_sum_d(acc, sbuf);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+int stream_red_blocks() { return 2 * num_sms(); }
+
+cudaError_t launch_norm_sq(const TensorView& v, double* parts, double* out, cudaStream_t st) {
+    const int G = stream_red_blocks();
+    if (v.dtype == NTF_F32)
+        k_norm_sq<float><<<G, kStreamRedThreads, 0, st>>>(static_cast<const float*>(v.data), v.rows(), v.C, v.ld,
+                                                          parts);
+    else
+        k_norm_sq<__nv_bfloat16><<<G, kStreamRedThreads, 0, st>>>(static_cast<const __nv_bfloat16*>(v.data),
+                                                                  v.rows(), v.C, v.ld, parts);
+    count_launch();
+    k_sum_parts<<<1, 256, 0, st>>>(parts, G, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// residual: warp per row (o, i); KR row = W(o,:) * A_{N-2}(i,:) in shared memory
+template <typename TE>
+__global__ void __launch_bounds__(kStreamRedThreads) k_residual_sq(const TE* __restrict__ T, int64_t Ii, int64_t n_o,
+                                                                   int64_t C, int64_t ld, int r,
+                                                                   const float* __restrict__ W, int RP,
+                                                                   const float* __restrict__ Ai,
+                                                                   const float* __restrict__ Ac,
+                                                                   double* __restrict__ parts) {
+    __shared__ double sbuf[33];
+    __shared__ float kr_s[kStreamRedThreads / 32][NTF_MAX_RANK];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t warp_g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t rows = Ii * n_o;
+    double acc = 0.0;
+    for (int64_t row = warp_g; row < rows; row += nwarps) {
+        const int64_t o = row / Ii, i = row % Ii;
+        __syncwarp();
+        for (int p = lane; p < r; p += 32) kr_s[wl][p] = W[o * RP + p] * Ai[i * r + p];
+        __syncwarp();
+        const TE* rp = T + row * ld;
+        float s = 0.f;
+        int cnt = 0;
+        for (int64_t c = lane; c < C; c += 32) {
+            float x = 0.f;
+            for (int p = 0; p < r; ++p) x = fmaf(kr_s[wl][p], __ldg(Ac + c * r + p), x);
+            const float d = load_elem<TE>(rp + c) - x;
+            s = fmaf(d, d, s);
+            if (++cnt == 64) { acc += (double)s; s = 0.f; cnt = 0; }
+        }
+        acc += (double)s;
+    }
+    const double tot = block_sum_d(acc, sbuf);
+    if (threadIdx.x == 0) parts[blockIdx.x] = tot;
+}
+
+cudaError_t launch_residual_sq(const TensorView& v, int r, const float* W, int RP, const float* Ai, const float* Ac,
+                               double* parts, double* out, cudaStream_t st) {
+    const int G = stream_red_blocks();
+    if (v.dtype == NTF_F32)
+        k_residual_sq<float><<<G, kStreamRedThreads, 0, st>>>(static_cast<const float*>(v.data), v.Ii, v.n_o, v.C,
+                                                              v.ld, r, W, RP, Ai, Ac, parts);
+    else
+        k_residual_sq<__nv_bfloat16><<<G, kStreamRedThreads, 0, st>>>(
+            static_cast<const __nv_bfloat16*>(v.data), v.Ii, v.n_o, v.C, v.ld, r, W, RP, Ai, Ac, parts);
+    count_launch();
+    k_sum_parts<<<1, 256, 0, st>>>(parts, G, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a8: bf16 cast with row pitch
+// ---------------------------------------------------------------------------
+__global__ void k_to_bf16(const float* __restrict__ src, int64_t rows, int64_t C, int64_t ld_src,
+                          __nv_bfloat16* __restrict__ dst, int64_t ld_dst) {
+    const int64_t n = rows * ld_dst;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = idx / ld_dst, c = idx % ld_dst;
+        dst[idx] = c < C ? __float2bfloat16_rn(src[row * ld_src + c]) : __float2bfloat16_rn(0.f);
+    }
+}
+
+cudaError_t launch_to_bf16(const float* src, int64_t rows, int64_t C, int64_t ld_src, void* dst, int64_t ld_dst,
+                           cudaStream_t st) {
+    int64_t g = (rows * ld_dst + 255) / 256;
+    if (g > 8 * num_sms()) g = 8 * num_sms();
+    if (g < 1) g = 1;
+    k_to_bf16<<<(int)g, 256, 0, st>>>(src, rows, C, ld_src, static_cast<__nv_bfloat16*>(dst), ld_dst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// a6: HER state, decision and the factor copies
+// ---------------------------------------------------------------------------
+__global__ void k_her_init(ntf_her_state* s, double beta0, double gamma, double gamma_bar, double eta,
+                           const double* f0) {
+    s->beta = beta0;
+    s->beta_bar = 1.0;
+    s->f_hat_prev = *f0;
+    s->gamma = gamma;
+    s->gamma_bar = gamma_bar;
+    s->eta = eta;
+    s->iters = 0;
+    s->restarts = 0;
+    s->last_restart = 0;
+    s->numeric_error = isfinite(*f0) ? 0 : 1;
+}
+
+cudaError_t launch_her_init(ntf_her_state* s, double beta0, double gamma, double gamma_bar, double eta,
+                            const double* f0, cudaStream_t st) {
+    k_her_init<<<1, 1, 0, st>>>(s, beta0, gamma, gamma_bar, eta, f0);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Alg. 2, restart test (F-hat_k > F-hat_{k-1}) and eqs. HER_eq:beta_update /
+// HER_eq:beta_bar_update.  A non-finite F-hat is treated as a restart and flagged.
+__global__ void k_her_decide(ntf_her_state* s, const double* fhat_p) {
+    const double fhat = *fhat_p;
+    const double beta = s->beta, beta_bar = s->beta_bar;
+    const bool finite = isfinite(fhat);
+    const bool restart = !finite || fhat > s->f_hat_prev;
+    if (restart) {
+        s->beta_bar = beta;
+        s->beta = beta / s->eta;
+    } else {
+        s->beta_bar = fmin(1.0, s->gamma_bar * beta_bar);
+        s->beta = fmin(beta_bar, s->gamma * beta);
+    }
+    s->f_hat_prev = fhat;
+    s->iters += 1;
+    s->restarts += restart ? 1 : 0;
+    s->last_restart = restart ? 1 : 0;
+    if (!finite) s->numeric_error = 1;
+}
+
+// restart: dst = A_hat side gets A (copy A -> A_hat); accept: A gets A_hat.
+__global__ void k_her_copy(const ntf_her_state* s, CopyPairs P) {
+    const bool restart = s->last_restart != 0;
+    for (int q = 0; q < P.count; ++q) {
+        float* a = P.a[q];
+        float* ah = P.ah[q];
+        const int64_t n = P.n[q];
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            if (restart) ah[i] = a[i];
+            else a[i] = ah[i];
+        }
+    }
+    for (int q = 0; q < P.gcount; ++q) {
+        double* g = P.g[q];
+        double* gh = P.gh[q];
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.gn; i += gridDim.x * blockDim.x) {
+            if (restart) gh[i] = g[i];
+            else g[i] = gh[i];
+        }
+    }
+}
+
+cudaError_t launch_her_step(ntf_her_state* s, const double* fhat, const CopyPairs& P, cudaStream_t st) {
+    k_her_decide<<<1, 1, 0, st>>>(s, fhat);
+    count_launch();
+    int64_t maxn = P.gn;
+    for (int q = 0; q < P.count; ++q) maxn = P.n[q] > maxn ? P.n[q] : maxn;
+    int64_t g = (maxn + 255) / 256;
+    if (g > 256) g = 256;
+    if (g < 1) g = 1;
+    k_her_copy<<<(int)g, 256, 0, st>>>(s, P);
+    count_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace ntf

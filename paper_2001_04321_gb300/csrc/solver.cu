@@ -1,0 +1,495 @@
+// Device-resident solver: Alg. 1 (plain BCD) and Alg. 2 (HER) with HALS or
+// projected-gradient block updates.  One outer iteration is a fixed sequence
+// of kernels on one stream with no host round trip (the restart decision is
+// taken on the device), so it can also be replayed as a CUDA graph.
+#include "small.cuh"
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace ntf {
+
+struct Solver {
+    TensorView vu;           // tensor as given (quality is reported against it)
+    TensorView vs;           // tensor streamed by the MTTKRP (vu or its bf16 copy)
+    void* bf16_copy = nullptr;
+    void* owned_T = nullptr; // device copy made by ntf_solve_host
+    int N = 0, r = 0;
+    ntf_opts o;
+    float* A[NTF_MAX_ORDER] = {nullptr};
+    float* Ah[NTF_MAX_ORDER] = {nullptr};
+    double* G[NTF_MAX_ORDER] = {nullptr};   // Grams of A
+    double* Gh[NTF_MAX_ORDER] = {nullptr};  // Grams of A_hat
+    float* Aprev = nullptr;
+    float* M = nullptr;
+    double* V = nullptr;
+    double* scal = nullptr;  // [0] ||T_s||^2 [1] F-hat [2] f_true [3] F-hat_0 [4] ||T_u||^2
+    ntf_her_state* her = nullptr;
+    void* ws_mt = nullptr;
+    void* ws_bcd = nullptr;
+    void* ws_res = nullptr;
+    size_t ws_res_bytes = 0;
+    MttkrpPlan plan[NTF_MAX_ORDER];
+    TmapCache tm[NTF_MAX_ORDER];
+    std::vector<void*> allocs;
+    int iters_done = 0;
+    double seconds = 0.0;
+    // timing of the streaming kernels
+    bool timing = false;
+    std::vector<StreamTimer> ev;
+    size_t ev_used = 0;
+    // graph replay
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+
+    ~Solver() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        for (auto& t : ev) {
+            if (t.start) cudaEventDestroy(t.start);
+            if (t.stop) cudaEventDestroy(t.stop);
+        }
+        for (void* p : allocs) cudaFree(p);
+    }
+
+    ntf_status alloc(void** p, size_t bytes) {
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return fail(NTF_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) + ") failed");
+        }
+        allocs.push_back(*p);
+        return NTF_OK;
+    }
+
+    StreamTimer* next_timer() {
+        if (!timing) return nullptr;
+        if (ev_used == ev.size()) {
+            StreamTimer t;
+            if (cudaEventCreate(&t.start) != cudaSuccess || cudaEventCreate(&t.stop) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            ev.push_back(t);
+        }
+        return &ev[ev_used++];
+    }
+
+    // one outer iteration of Alg. 2 (or Alg. 1 when her == 0)
+    ntf_status iterate(cudaStream_t st) {
+        const bool use_her = o.her != 0;
+        for (int n = 0; n < N; ++n) {
+            const int64_t rows = vs.dims[n];
+            GramPtrs gp{};
+            for (int l = 0; l < N; ++l) gp.g[l] = Gh[l];
+            cudaError_t e = launch_hadamard(gp, N, n, r, V, st);
+            if (e != cudaSuccess) return cuda_fail(e, "hadamard");
+            const float* fac[NTF_MAX_ORDER];
+            for (int l = 0; l < N; ++l) fac[l] = Ah[l];
+            ntf_status s = run_mttkrp(vs, plan[n], fac, M, ws_mt, st, &tm[n], next_timer());
+            if (s != NTF_OK) return s;
+            if (use_her) NTF_CUDA_TRY(cudaMemcpyAsync(Aprev, A[n], sizeof(float) * rows * r, cudaMemcpyDeviceToDevice, st));
+            e = launch_bcd(o.method == NTF_HALS ? 0 : 1, A[n], rows, r, M, V, o.inner_max, o.inner_tol, ws_bcd, st);
+            if (e != cudaSuccess) return cuda_fail(e, "block update");
+            if (use_her) {
+                e = launch_extrapolate(A[n], Aprev, &her->beta, rows * r, Ah[n], st);
+                if (e != cudaSuccess) return cuda_fail(e, "extrapolate");
+                e = launch_gram(A[n], rows, r, G[n], st);
+                if (e != cudaSuccess) return cuda_fail(e, "gram");
+            }
+            e = launch_gram(Ah[n], rows, r, Gh[n], st);
+            if (e != cudaSuccess) return cuda_fail(e, "gram");
+        }
+        // F-hat_k = ||T||^2 - 2 <M_{N-1}, A_{N-1}> + sum(V_{N-1} (*) G(A_{N-1}))   (Alg. 2, line 9)
+        const int last = N - 1;
+        cudaError_t e = launch_objective(&scal[0], M, A[last], vs.dims[last], r, V, &scal[1], nullptr, st);
+        if (e != cudaSuccess) return cuda_fail(e, "objective");
+        if (use_her) {
+            CopyPairs P;
+            P.count = N;
+            P.gcount = N;
+            P.gn = r * r;
+            for (int l = 0; l < N; ++l) {
+                P.a[l] = A[l];
+                P.ah[l] = Ah[l];
+                P.n[l] = vs.dims[l] * r;
+                P.g[l] = G[l];
+                P.gh[l] = Gh[l];
+            }
+            e = launch_her_step(her, &scal[1], P, st);
+            if (e != cudaSuccess) return cuda_fail(e, "her step");
+        }
+        return NTF_OK;
+    }
+
+    ntf_status residual(const TensorView& v, double* out, cudaStream_t st) {
+        const int RP = (int)round_up(r, 4);
+        float* W = static_cast<float*>(ws_res);
+        const size_t woff = ((sizeof(float) * (size_t)v.n_o * RP) + 255) & ~size_t(255);
+        double* parts = reinterpret_cast<double*>(static_cast<unsigned char*>(ws_res) + woff);
+        const float* fac[NTF_MAX_ORDER];
+        for (int l = 0; l < N; ++l) fac[l] = A[l];
+        cudaError_t e = launch_weights_all(v, fac, r, RP, W, st);
+        if (e != cudaSuccess) return cuda_fail(e, "residual weights");
+        e = launch_residual_sq(v, r, W, RP, A[N - 2], A[N - 1], parts, out, st);
+        if (e != cudaSuccess) return cuda_fail(e, "residual");
+        return NTF_OK;
+    }
+};
+
+static ntf_status validate_opts(const ntf_opts& o) {
+    if (o.her != 0 && o.her != 1) return fail(NTF_EINVAL, "opts.her must be 0 or 1");
+    if (o.method != NTF_HALS && o.method != NTF_PGD) return fail(NTF_EINVAL, "opts.method unknown");
+    if (o.inner_max < 1) return fail(NTF_EINVAL, "opts.inner_max must be >= 1");
+    if (!(o.inner_tol >= 0.0)) return fail(NTF_EINVAL, "opts.inner_tol must be >= 0");
+    if (o.max_iters < 0) return fail(NTF_EINVAL, "opts.max_iters must be >= 0");
+    if (o.compute_dtype != NTF_F32 && o.compute_dtype != NTF_BF16) return fail(NTF_EINVAL, "opts.compute_dtype unknown");
+    if (o.her) {
+        if (!(o.beta0 > 0.0 && o.beta0 <= 1.0)) return fail(NTF_EINVAL, "opts.beta0 must be in (0, 1]");
+        if (!(1.0 <= o.gamma_bar && o.gamma_bar <= o.gamma && o.gamma <= o.eta))
+            return fail(NTF_EINVAL, "need 1 <= gamma_bar <= gamma <= eta (Sec. 3.1, eq. HER:relation)");
+    }
+    return NTF_OK;
+}
+
+static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const* factors, int rank,
+                                const ntf_opts* opts, cudaStream_t st, void* owned_T) {
+    *out = nullptr;
+    Solver* S = new Solver();
+    S->owned_T = owned_T;
+    if (owned_T) S->allocs.push_back(owned_T);
+    auto bail = [&](ntf_status s) {
+        delete S;
+        return s;
+    };
+    ntf_status s = make_view(T, &S->vu);
+    if (s != NTF_OK) return bail(s);
+    if (rank < 1 || rank > NTF_MAX_RANK) return bail(fail(NTF_EINVAL, "rank must be in [1, 64]"));
+    if (!factors) return bail(fail(NTF_EINVAL, "factors is NULL"));
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, S->vu.data) != cudaSuccess ||
+        (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return bail(fail(NTF_EINVAL, "tensor data must be device memory"));
+    }
+    for (int l = 0; l < S->vu.order; ++l) {
+        if (!factors[l] || cudaPointerGetAttributes(&pa, factors[l]) != cudaSuccess ||
+            (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return bail(fail(NTF_EINVAL, "factors must be device memory"));
+        }
+    }
+    if (opts) S->o = *opts;
+    else ntf_opts_default(&S->o);
+    s = validate_opts(S->o);
+    if (s != NTF_OK) return bail(s);
+    S->N = S->vu.order;
+    S->r = rank;
+    const int N = S->N, r = rank;
+
+    // streamed tensor
+    S->vs = S->vu;
+    if (S->o.compute_dtype == NTF_BF16 && S->vu.dtype == NTF_F32) {
+        const int64_t ldb = round_up(S->vu.C, 8);
+        s = S->alloc(&S->bf16_copy, sizeof(uint16_t) * (size_t)S->vu.rows() * ldb);
+        if (s != NTF_OK) return bail(s);
+        cudaError_t e = launch_to_bf16(static_cast<const float*>(S->vu.data), S->vu.rows(), S->vu.C, S->vu.ld,
+                                       S->bf16_copy, ldb, st);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "bf16 cast"));
+        S->vs.dtype = NTF_BF16;
+        S->vs.es = 2;
+        S->vs.ld = ldb;
+        S->vs.data = S->bf16_copy;
+    }
+
+    int64_t maxrows = 0;
+    for (int l = 0; l < N; ++l) maxrows = std::max(maxrows, S->vu.dims[l]);
+    for (int l = 0; l < N; ++l) {
+        const size_t fb = sizeof(float) * (size_t)S->vu.dims[l] * r;
+        if ((s = S->alloc((void**)&S->A[l], fb)) != NTF_OK) return bail(s);
+        NTF_CUDA_TRY(cudaMemcpyAsync(S->A[l], factors[l], fb, cudaMemcpyDeviceToDevice, st));
+        if ((s = S->alloc((void**)&S->G[l], sizeof(double) * r * r)) != NTF_OK) return bail(s);
+        if (S->o.her) {
+            if ((s = S->alloc((void**)&S->Ah[l], fb)) != NTF_OK) return bail(s);
+            NTF_CUDA_TRY(cudaMemcpyAsync(S->Ah[l], factors[l], fb, cudaMemcpyDeviceToDevice, st));  // A_hat_0 = A_0
+            if ((s = S->alloc((void**)&S->Gh[l], sizeof(double) * r * r)) != NTF_OK) return bail(s);
+        } else {
+            S->Ah[l] = S->A[l];
+            S->Gh[l] = S->G[l];
+        }
+    }
+    if ((s = S->alloc((void**)&S->Aprev, sizeof(float) * maxrows * r)) != NTF_OK) return bail(s);
+    if ((s = S->alloc((void**)&S->M, sizeof(float) * maxrows * r)) != NTF_OK) return bail(s);
+    if ((s = S->alloc((void**)&S->V, sizeof(double) * r * r)) != NTF_OK) return bail(s);
+    if ((s = S->alloc((void**)&S->scal, sizeof(double) * 8)) != NTF_OK) return bail(s);
+    if ((s = S->alloc((void**)&S->her, sizeof(ntf_her_state))) != NTF_OK) return bail(s);
+    size_t ws = 0;
+    for (int n = 0; n < N; ++n) {
+        if ((s = plan_mttkrp(S->vs, r, n, &S->plan[n])) != NTF_OK) return bail(s);
+        if ((s = configure_mttkrp(S->vs, S->plan[n])) != NTF_OK) return bail(s);
+        ws = std::max(ws, S->plan[n].total);
+    }
+    if ((s = S->alloc(&S->ws_mt, ws)) != NTF_OK) return bail(s);
+    if ((s = S->alloc(&S->ws_bcd, bcd_workspace(maxrows))) != NTF_OK) return bail(s);
+    S->ws_res_bytes = (((sizeof(float) * (size_t)S->vu.n_o * round_up(r, 4)) + 255) & ~size_t(255)) +
+                      sizeof(double) * (size_t)std::max(stream_red_blocks(), 1);
+    if ((s = S->alloc(&S->ws_res, S->ws_res_bytes)) != NTF_OK) return bail(s);
+    if (!device_error_word()) return bail(fail(NTF_ECUDA, "device error word unavailable"));
+    {
+        cudaError_t e0 = launch_objective(nullptr, nullptr, nullptr, 1, r, nullptr, nullptr, nullptr, st);
+        if (e0 != cudaSuccess) return bail(cuda_fail(e0, "configure objective kernel"));
+    }
+
+    // ||T||^2 of the streamed and of the given tensor
+    double* parts = reinterpret_cast<double*>(static_cast<unsigned char*>(S->ws_res) +
+                                              ((((sizeof(float) * (size_t)S->vu.n_o * round_up(r, 4)) + 255)) &
+                                               ~size_t(255)));
+    cudaError_t e = launch_norm_sq(S->vs, parts, &S->scal[0], st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "norm"));
+    e = launch_norm_sq(S->vu, parts, &S->scal[4], st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "norm"));
+    // Grams of A_0 (= A_hat_0)
+    for (int l = 0; l < N; ++l) {
+        e = launch_gram(S->A[l], S->vu.dims[l], r, S->G[l], st);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "gram"));
+        if (S->o.her) NTF_CUDA_TRY(cudaMemcpyAsync(S->Gh[l], S->G[l], sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+    }
+    // F-hat_0 = ||T - [[A_0]]||^2 explicitly (on the streamed tensor)
+    if ((s = S->residual(S->vs, &S->scal[3], st)) != NTF_OK) return bail(s);
+    e = launch_her_init(S->her, S->o.beta0, S->o.gamma, S->o.gamma_bar, S->o.eta, &S->scal[3], st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "her init"));
+    NTF_CUDA_TRY(cudaMemcpyAsync(&S->scal[1], &S->scal[3], sizeof(double), cudaMemcpyDeviceToDevice, st));
+    *out = S;
+    return NTF_OK;
+}
+
+static ntf_status run_solver(Solver* S, int iters, cudaStream_t st) {
+    if (iters < 0) return fail(NTF_EINVAL, "iters must be >= 0");
+    const bool graph = S->o.use_graph && st != nullptr && !S->timing;
+    for (int k = 0; k < iters; ++k) {
+        if (graph) {
+            if (!S->gexec || S->gstream != st) {
+                if (S->gexec) {
+                    cudaGraphExecDestroy(S->gexec);
+                    S->gexec = nullptr;
+                }
+                cudaGraph_t g;
+                NTF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                ntf_status s = S->iterate(st);
+                cudaError_t e = cudaStreamEndCapture(st, &g);
+                if (s != NTF_OK) return s;
+                if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+                e = cudaGraphInstantiate(&S->gexec, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+                S->gstream = st;
+            }
+            NTF_CUDA_TRY(cudaGraphLaunch(S->gexec, st));
+        } else {
+            ntf_status s = S->iterate(st);
+            if (s != NTF_OK) return s;
+        }
+        ++S->iters_done;
+    }
+    return NTF_OK;
+}
+
+static ntf_status solver_report(Solver* S, ntf_report* rep, cudaStream_t st) {
+    ntf_status s = S->residual(S->vu, &S->scal[2], st);
+    if (s != NTF_OK) return s;
+    double h[8];
+    ntf_her_state hs;
+    NTF_CUDA_TRY(cudaMemcpyAsync(h, S->scal, sizeof(h), cudaMemcpyDeviceToHost, st));
+    NTF_CUDA_TRY(cudaMemcpyAsync(&hs, S->her, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    NTF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (rep) {
+        rep->iters = S->iters_done;
+        rep->restarts = S->o.her ? hs.restarts : 0;
+        rep->f_hat_last = h[1];
+        rep->f_true_last = h[2];
+        rep->tnorm_sq = h[4];
+        rep->rel_error = h[4] > 0 ? std::sqrt(std::max(h[2], 0.0) / h[4]) : 0.0;
+        rep->beta_last = S->o.her ? hs.beta : 0.0;
+        rep->beta_bar_last = S->o.her ? hs.beta_bar : 0.0;
+        rep->seconds = S->seconds;
+    }
+    if ((S->o.her && hs.numeric_error) || !std::isfinite(h[1]) || !std::isfinite(h[2]))
+        return fail(NTF_ENUMERIC, "non-finite objective encountered");
+    return NTF_OK;
+}
+
+}  // namespace ntf
+
+using namespace ntf;
+
+struct ntf_solver {
+    Solver* s;
+};
+
+extern "C" {
+
+ntf_status ntf_solver_create(ntf_solver** out, const ntf_tensor* T, float* const* factors, int rank,
+                             const ntf_opts* opts, void* stream) {
+    if (!out) return fail(NTF_EINVAL, "out is NULL");
+    *out = nullptr;
+    Solver* S = nullptr;
+    ntf_status s = create_solver(&S, T, factors, rank, opts, static_cast<cudaStream_t>(stream), nullptr);
+    if (s != NTF_OK) return s;
+    *out = new ntf_solver{S};
+    return NTF_OK;
+}
+
+ntf_status ntf_solver_run(ntf_solver* h, int iters, void* stream) {
+    if (!h || !h->s) return fail(NTF_EINVAL, "solver is NULL");
+    return run_solver(h->s, iters, static_cast<cudaStream_t>(stream));
+}
+
+ntf_status ntf_solver_get_factors(ntf_solver* h, float* const* factors, void* stream) {
+    if (!h || !h->s) return fail(NTF_EINVAL, "solver is NULL");
+    if (!factors) return fail(NTF_EINVAL, "factors is NULL");
+    Solver* S = h->s;
+    for (int l = 0; l < S->N; ++l) {
+        if (!factors[l]) return fail(NTF_EINVAL, "factor pointer is NULL");
+        NTF_CUDA_TRY(cudaMemcpyAsync(factors[l], S->A[l], sizeof(float) * S->vu.dims[l] * S->r,
+                                     cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+    }
+    return NTF_OK;
+}
+
+ntf_status ntf_solver_report(ntf_solver* h, ntf_report* report, void* stream) {
+    if (!h || !h->s) return fail(NTF_EINVAL, "solver is NULL");
+    return solver_report(h->s, report, static_cast<cudaStream_t>(stream));
+}
+
+ntf_status ntf_solver_set_timing(ntf_solver* h, int on) {
+    if (!h || !h->s) return fail(NTF_EINVAL, "solver is NULL");
+    h->s->timing = on != 0;
+    h->s->ev_used = 0;
+    return NTF_OK;
+}
+
+ntf_status ntf_solver_mttkrp_time(ntf_solver* h, double* total_ms, int64_t* launches, double* bytes_per_launch,
+                                  void* stream) {
+    if (!h || !h->s) return fail(NTF_EINVAL, "solver is NULL");
+    Solver* S = h->s;
+    NTF_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    double tot = 0.0;
+    for (size_t i = 0; i < S->ev_used; ++i) {
+        float ms = 0.f;
+        NTF_CUDA_TRY(cudaEventElapsedTime(&ms, S->ev[i].start, S->ev[i].stop));
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = (int64_t)S->ev_used;
+    if (bytes_per_launch) *bytes_per_launch = (double)S->vs.numel() * S->vs.es;
+    S->ev_used = 0;
+    return NTF_OK;
+}
+
+void ntf_solver_destroy(ntf_solver* h) {
+    if (!h) return;
+    delete h->s;
+    delete h;
+}
+
+ntf_status ntf_solve(const ntf_tensor* T, float* const* factors, int rank, const ntf_opts* opts, ntf_report* report,
+                     void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Solver* S = nullptr;
+    ntf_status s = create_solver(&S, T, factors, rank, opts, st, nullptr);
+    if (s != NTF_OK) return s;
+    NTF_CUDA_TRY(cudaStreamSynchronize(st));
+    auto t0 = std::chrono::steady_clock::now();
+    s = run_solver(S, S->o.max_iters, st);
+    if (s == NTF_OK) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "solve");
+    }
+    S->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (s == NTF_OK) {
+        for (int l = 0; l < S->N && s == NTF_OK; ++l) {
+            cudaError_t e = cudaMemcpyAsync(factors[l], S->A[l], sizeof(float) * S->vu.dims[l] * rank,
+                                            cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) s = cuda_fail(e, "copy factors");
+        }
+    }
+    if (s == NTF_OK) s = solver_report(S, report, st);
+    delete S;
+    if (s == NTF_OK) s = ntf_device_status(stream);
+    return s;
+}
+
+ntf_status ntf_solve_host(const ntf_tensor* T_host, float* const* factors_host, int rank, const ntf_opts* opts,
+                          ntf_report* report, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!T_host || !factors_host) return fail(NTF_EINVAL, "T_host and factors_host must not be NULL");
+    if (T_host->order < 2 || T_host->order > NTF_MAX_ORDER) return fail(NTF_EINVAL, "order must be in [2, 8]");
+    if (!T_host->data) return fail(NTF_EINVAL, "tensor data is NULL");
+    if (rank < 1 || rank > NTF_MAX_RANK) return fail(NTF_EINVAL, "rank must be in [1, 64]");
+    ntf_tensor Td = *T_host;
+    const int es = T_host->dtype == NTF_F32 ? 4 : 2;
+    const int64_t ld = T_host->ld ? T_host->ld : T_host->dims[T_host->order - 1];
+    int64_t rows = 1;
+    for (int l = 0; l < T_host->order - 1; ++l) rows *= T_host->dims[l];
+    // device copy with 16-byte rows
+    const int64_t ldd = round_up(T_host->dims[T_host->order - 1], 16 / es);
+    void* dT = nullptr;
+    cudaError_t e = cudaMalloc(&dT, (size_t)rows * ldd * es);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(NTF_ENOMEM, "cudaMalloc for the tensor failed");
+    }
+    e = cudaMemcpy2DAsync(dT, ldd * es, T_host->data, ld * es, T_host->dims[T_host->order - 1] * es, rows,
+                          cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        cudaFree(dT);
+        return cuda_fail(e, "tensor upload");
+    }
+    Td.data = dT;
+    Td.ld = ldd;
+    std::vector<float*> dF(T_host->order, nullptr);
+    auto cleanup = [&]() {
+        for (float* p : dF) cudaFree(p);
+    };
+    for (int l = 0; l < T_host->order; ++l) {
+        const size_t fb = sizeof(float) * (size_t)T_host->dims[l] * rank;
+        if (!factors_host[l]) {
+            cleanup();
+            cudaFree(dT);
+            return fail(NTF_EINVAL, "factor pointer is NULL");
+        }
+        if (cudaMalloc(&dF[l], fb) != cudaSuccess) {
+            cudaGetLastError();
+            cleanup();
+            cudaFree(dT);
+            return fail(NTF_ENOMEM, "cudaMalloc for a factor failed");
+        }
+        cudaMemcpyAsync(dF[l], factors_host[l], fb, cudaMemcpyHostToDevice, st);
+    }
+    Solver* S = nullptr;
+    ntf_status s = create_solver(&S, &Td, dF.data(), rank, opts, st, dT);  // S owns dT
+    if (s != NTF_OK) {
+        cleanup();
+        cudaFree(dT);
+        return s;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    s = run_solver(S, S->o.max_iters, st);
+    if (s == NTF_OK) {
+        for (int l = 0; l < S->N; ++l)
+            cudaMemcpyAsync(factors_host[l], S->A[l], sizeof(float) * S->vu.dims[l] * rank, cudaMemcpyDeviceToHost, st);
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "solve");
+    }
+    S->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (s == NTF_OK) s = solver_report(S, report, st);
+    delete S;
+    cleanup();
+    if (s == NTF_OK) s = ntf_device_status(stream);
+    return s;
+}
+
+}  // extern "C"

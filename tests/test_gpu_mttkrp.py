@@ -1,0 +1,93 @@
+"""MTTKRP (step a1) parity: CUDA path vs the FP64 oracle, element by element.
+
+Tolerances: FP32 storage, rel. Frobenius <= 1e-5 against the oracle on the
+same FP32 tensor.  BF16 storage: <= 1e-5 against the oracle on the same
+bf16-rounded tensor (the kernel reads exact bf16 values and accumulates in
+FP32) and <= 2e-2 against the FP32 tensor.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import device_tensor, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [
+    ((37, 23, 19), 5),        # ragged in every mode
+    ((20, 20, 20), 5),        # the 20^3 workload shape
+    ((64, 128, 64), 16),      # exact tiles
+    ((130, 300, 70), 20),     # several tiles per mode + ragged tails
+    ((5, 7, 200), 1),         # rank 1, long last mode
+    ((3, 4, 5, 6), 7),        # 4-way: two outer modes
+    ((6, 5, 4, 3, 33), 12),   # 5-way
+    ((40, 50), 9),            # 2-way (NMF)
+    ((33, 17, 65), 40),       # rank > 32: two column blocks
+    ((9, 300, 33), 64),       # maximum rank
+    ((1, 1, 1), 3),           # degenerate
+    ((2, 1, 130), 2),
+    ((1, 200, 1), 4),
+]
+
+
+def _problem(dims, r, seed):
+    T, _ = synth.make_tensor(dims, r, 1e-2, seed=seed)
+    F = synth.make_init(dims, r, seed=seed)
+    return T, F
+
+
+@pytest.mark.parametrize("dims,r", SHAPES)
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_mttkrp_matches_oracle(dims, r, dtype):
+    import torch
+    import paper_2001_04321_gb300 as ntf
+    T, F = _problem(dims, r, seed=len(dims) * 100 + r)
+    buf, d, ld = device_tensor(T, dtype)
+    Fd = [torch.from_numpy(A).cuda() for A in F]
+    if dtype == "bf16":
+        Tq = oracle.bf16_to_f64(oracle.round_bf16(T))
+    for n in range(len(dims)):
+        M = ntf.mttkrp(buf, Fd, n, dims=d, ld=ld).cpu().numpy()
+        if dtype == "f32":
+            assert rel_fro(M, oracle.mttkrp(T, F, n)) <= 1e-5, (dims, r, n)
+        else:
+            assert rel_fro(M, oracle.mttkrp(Tq, F, n)) <= 1e-5, (dims, r, n)
+            assert rel_fro(M, oracle.mttkrp(T, F, n)) <= 2e-2, (dims, r, n)
+
+
+def test_mttkrp_is_bitwise_reproducible_and_ignores_row_padding():
+    import torch
+    import paper_2001_04321_gb300 as ntf
+    dims, r = (50, 70, 45), 12
+    T, F = _problem(dims, r, 5)
+    Fd = [torch.from_numpy(A).cuda() for A in F]
+    buf, d, ld = device_tensor(T, "f32")
+    nan_buf, _, _ = device_tensor(T, "f32", pad_value=float("nan"))   # padding holds NaN
+    for n in range(3):
+        a = ntf.mttkrp(buf, Fd, n, dims=d, ld=ld).cpu().numpy()
+        b = ntf.mttkrp(buf, Fd, n, dims=d, ld=ld).cpu().numpy()
+        c = ntf.mttkrp(nan_buf, Fd, n, dims=d, ld=ld).cpu().numpy()
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_mttkrp_rejects_bad_arguments():
+    import torch
+    import paper_2001_04321_gb300 as ntf
+    T = torch.rand(4, 5, 8, device="cuda")
+    F = [torch.rand(4, 3, device="cuda"), torch.rand(5, 3, device="cuda"), torch.rand(8, 3, device="cuda")]
+    with pytest.raises(ntf.NTFError) as e:
+        ntf.mttkrp(T, F, 3)
+    assert e.value.status == 1
+    host_F = [F[0], F[1].cpu().contiguous(), F[2]]
+    with pytest.raises(ntf.NTFError):
+        ntf.mttkrp(T, host_F, 0)                     # host pointer as a factor
+    odd = torch.rand(4, 5, 7, device="cuda")         # 28-byte rows: not 16-byte aligned
+    with pytest.raises(ntf.NTFError) as e:
+        ntf.mttkrp(odd, F[:2] + [torch.rand(7, 3, device="cuda")], 0)
+    assert "16 bytes" in str(e.value)
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ntf.NTFError) as e:
+        ntf.mttkrp(T, F, 0, workspace=ws)
+    assert "workspace" in str(e.value)
+    ntf.device_status()
