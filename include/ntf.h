@@ -174,6 +174,29 @@ NTF_API size_t ntf_mttkrp_workspace_bytes(const ntf_tensor* T, int rank, int mod
 NTF_API ntf_status ntf_mttkrp(const ntf_tensor* T, const float* const* factors, int rank, int mode, float* out,
                       void* workspace, size_t ws_bytes, void* stream);
 
+/* Size of the fixed device scratch used by ntf_mttkrp_noalloc (per device). */
+#define NTF_MTTKRP_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* ntf_mttkrp without a workspace argument and without any allocation.  The
+ * paper has no counterpart: this entry exists for callers that cannot
+ * allocate device memory -- code inside a host application that owns all
+ * device memory through its own allocator, latency-critical loops where
+ * cudaMalloc/cudaFree (which can block and synchronise the device) are not
+ * acceptable, and processes that must not grow their device footprint per
+ * call.  Same arguments, layout, result and errors as ntf_mttkrp, minus the
+ * workspace.  Scratch comes from one fixed array of
+ * NTF_MTTKRP_NOALLOC_SCRATCH_BYTES (16 MiB) that every GPU loading the library
+ * holds until the process exits; requests needing more (see
+ * ntf_mttkrp_workspace_bytes) fail with NTF_EINVAL and a message, nothing
+ * launched.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents (nothing in it needs to start at zero): calls that
+ * overlap on the GPU -- on different streams without ordering, or from
+ * several host threads -- race and give wrong results, so order them. */
+NTF_API ntf_status ntf_mttkrp_noalloc(const ntf_tensor* T, const float* const* factors, int rank, int mode,
+                                      float* out, void* stream);
+
 /* ----------------------------------------------------------------------- */
 /* Step a2: Grams and Hadamard product of Grams                              */
 /* ----------------------------------------------------------------------- */

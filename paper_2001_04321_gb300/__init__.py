@@ -77,6 +77,7 @@ _SIGS = {
     "ntf_tensor_norm_sq": (C.c_int, [C.POINTER(_Tensor), _P, _P, C.c_size_t, _P]),
     "ntf_mttkrp_workspace_bytes": (C.c_size_t, [C.POINTER(_Tensor), C.c_int, C.c_int]),
     "ntf_mttkrp": (C.c_int, [C.POINTER(_Tensor), C.POINTER(_P), C.c_int, C.c_int, _P, _P, C.c_size_t, _P]),
+    "ntf_mttkrp_noalloc": (C.c_int, [C.POINTER(_Tensor), C.POINTER(_P), C.c_int, C.c_int, _P, _P]),
     "ntf_gram": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P]),
     "ntf_hadamard_grams": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int, C.c_int, _P, _P]),
     "ntf_bcd_workspace_bytes": (C.c_size_t, [C.c_int64, C.c_int]),
