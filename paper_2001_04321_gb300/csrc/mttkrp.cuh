@@ -2,6 +2,7 @@
 #pragma once
 
 #include "ntf_common.cuh"
+#include "mttkrp_reduce.cuh"
 
 namespace ntf {
 
@@ -56,6 +57,7 @@ ntf_status run_mttkrp(const TensorView& v, const MttkrpPlan& plan, const float* 
                       void* workspace, cudaStream_t st, TmapCache* cache, StreamTimer* timer);
 
 int num_sms();
+ReduceParams make_reduce_params(const TensorView& v, const MttkrpPlan& P, const float* part, const float* W);
 ntf_status configure_mttkrp(const TensorView& v, const MttkrpPlan& P);
 
 }  // namespace ntf

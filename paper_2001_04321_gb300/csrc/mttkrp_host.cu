@@ -3,6 +3,8 @@
 //   pack factors -> weight table W -> streaming kernel -> reduction.
 #include "mttkrp.cuh"
 #include "mttkrp_kernels.cuh"
+#include "mttkrp_reduce.cuh"
+#include "epilogue.cuh"
 
 #include <cmath>
 #include <cstring>
@@ -165,7 +167,7 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     if (P.kind == ModeKind::Inner)
         part = (size_t)P.G * P.Smax * kStreamWarps * P.I_T * P.RP;
     else if (P.kind == ModeKind::Outer)
-        part = (size_t)v.n_o * P.nb * kStreamWarps * P.RP;
+        part = (size_t)v.n_o * P.nb * P.RP;
     else
         part = (size_t)P.G * P.Cpad * P.RP;
     off = align256(off + sizeof(float) * part);
@@ -218,68 +220,11 @@ __global__ void k_weights(FactorPtrs F, Dims D, int order, int skip, int r, int 
     }
 }
 
-struct ReduceParams {
-    int64_t n_tiles, n_ot, nb, Ii, n_o, C, Cpad;
-    int G, Smax, I_T, RP, r;
-    // outer mode
-    int64_t In, stride, hi_count;
-    const float* part;
-    const float* W;
-    float* out;
-};
-
-__global__ void k_reduce_inner(const ReduceParams P) {
-    const int64_t n = P.Ii * P.r;
+__global__ void k_reduce(const ReduceParams P, int64_t n_out, float* __restrict__ out) {
+    const int64_t n = n_out * P.r;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / P.r;
-        const int p = (int)(idx % P.r);
-        const int64_t ib = i / P.I_T;
-        const int b = (int)(i % P.I_T);
-        float s = 0.f;
-        for (int g = 0; g < P.G; ++g) {
-            const int64_t tb = (P.n_tiles * g) / P.G, te = (P.n_tiles * (g + 1)) / P.G;
-            if (te <= tb) continue;
-            const int64_t first = tb / P.n_ot, last = (te - 1) / P.n_ot;
-            if (ib < first || ib > last) continue;
-            const int seg = (int)(ib - first);
-            for (int w = 0; w < kStreamWarps; ++w)
-                s += P.part[((((int64_t)g * P.Smax + seg) * kStreamWarps + w) * P.I_T + b) * P.RP + p];
-        }
-        P.out[idx] = s;
-    }
-}
-
-__global__ void k_reduce_outer(const ReduceParams P) {
-    const int64_t n = P.In * P.r;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = idx / P.r;
-        const int p = (int)(idx % P.r);
-        float s = 0.f;
-        for (int64_t hi = 0; hi < P.hi_count; ++hi)
-            for (int64_t lo = 0; lo < P.stride; ++lo) {
-                const int64_t o = (hi * P.In + j) * P.stride + lo;
-                float so = 0.f;
-                for (int64_t ib = 0; ib < P.nb; ++ib)
-                    for (int w = 0; w < kStreamWarps; ++w)
-                        so += P.part[((o * P.nb + ib) * kStreamWarps + w) * P.RP + p];
-                s = fmaf(P.W[o * P.RP + p], so, s);
-            }
-        P.out[idx] = s;
-    }
-}
-
-__global__ void k_reduce_last(const ReduceParams P) {
-    const int64_t n = P.C * P.r;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = idx / P.r;
-        const int p = (int)(idx % P.r);
-        float s = 0.f;
-        for (int g = 0; g < P.G; ++g) s += P.part[((int64_t)g * P.Cpad + c) * P.RP + p];
-        P.out[idx] = s;
-    }
+         idx += (int64_t)gridDim.x * blockDim.x)
+        out[idx] = reduce_output(P, idx / P.r, (int)(idx % P.r));
 }
 
 static int grid_for(int64_t n, int threads) {
@@ -289,9 +234,103 @@ static int grid_for(int64_t n, int threads) {
     return (int)b;
 }
 
+ReduceParams make_reduce_params(const TensorView& v, const MttkrpPlan& P, const float* part, const float* W) {
+    ReduceParams R{};
+    R.kind = P.kind == ModeKind::Inner ? 0 : P.kind == ModeKind::Outer ? 1 : 2;
+    R.n_tiles = P.n_tiles;
+    R.n_ot = P.n_ot;
+    R.nb = P.nb;
+    R.Ii = v.Ii;
+    R.n_o = v.n_o;
+    R.C = v.C;
+    R.Cpad = P.Cpad;
+    R.G = P.G;
+    R.Smax = P.Smax;
+    R.I_T = P.I_T;
+    R.RP = P.RP;
+    R.r = P.rank;
+    R.part = part;
+    R.W = W;
+    if (P.kind == ModeKind::Outer) {
+        R.In = v.dims[P.mode];
+        int64_t stride = 1;
+        for (int l = P.mode + 1; l < v.order - 2; ++l) stride *= v.dims[l];
+        R.stride = stride;
+        R.hi_count = v.n_o / (R.In * stride);
+    }
+    return R;
+}
+
 // ---------------------------------------------------------------------------
 // launch sequence
 // ---------------------------------------------------------------------------
+static ntf_status get_tensor_map(const TensorView& v, const MttkrpPlan& P, TmapCache* cache, CUtensorMap* local,
+                                 const CUtensorMap** map) {
+    if (cache && cache->valid && cache->data == v.data && cache->I_T == P.I_T && cache->O_T == P.O_T) {
+        *map = &cache->map;
+        return NTF_OK;
+    }
+    const uint32_t box0 = 128 / v.es;
+    ntf_status s = encode_tensor_map_3d(local, v.dtype, v.data, (uint64_t)v.C, (uint64_t)v.Ii, (uint64_t)v.n_o,
+                                        (uint64_t)(v.ld * v.es), (uint64_t)(v.Ii * v.ld * v.es), box0,
+                                        (uint32_t)P.I_T, (uint32_t)P.O_T);
+    if (s != NTF_OK) return s;
+    *map = local;
+    if (cache) {
+        cache->valid = true;
+        cache->data = v.data;
+        cache->I_T = P.I_T;
+        cache->O_T = P.O_T;
+        cache->map = *local;
+        *map = &cache->map;
+    }
+    return NTF_OK;
+}
+
+ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* workspace, cudaStream_t st,
+                             TmapCache* cache, StreamTimer* timer) {
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    CUtensorMap local_map;
+    const CUtensorMap* map = nullptr;
+    ntf_status s = get_tensor_map(v, P, cache, &local_map, &map);
+    if (s != NTF_OK) return s;
+    StreamParams S{};
+    S.C = v.C;
+    S.Ii = v.Ii;
+    S.n_o = v.n_o;
+    S.I_T = P.I_T;
+    S.O_T = P.O_T;
+    S.nb = P.nb;
+    S.n_ot = P.n_ot;
+    S.n_tiles = P.n_tiles;
+    S.n_kc = P.n_kc;
+    S.RP = P.RP;
+    S.Smax = P.Smax;
+    S.Cpad = P.Cpad;
+    S.Fc = reinterpret_cast<const float*>(ws + P.off_Fc);
+    S.Fi = reinterpret_cast<const float*>(ws + P.off_Fi);
+    S.W = reinterpret_cast<const float*>(ws + P.off_W);
+    S.part = reinterpret_cast<float*>(ws + P.off_part);
+    S.err = device_error_word();
+    const int kind = P.kind == ModeKind::Inner ? 0 : P.kind == ModeKind::Outer ? 1 : 2;
+    dim3 grid;
+    size_t smem;
+    if (P.kind == ModeKind::Last) {
+        grid = dim3(P.G, P.n_cb, P.n_pb);
+        smem = stream_last_smem(v.es, P.R);
+    } else {
+        grid = dim3(P.G, P.n_pb, 1);
+        smem = stream_rows_smem(v.es, P.RP);
+    }
+    if (timer && timer->start) NTF_CUDA_TRY(cudaEventRecord(timer->start, st));
+    cudaError_t e = v.dtype == NTF_F32 ? launch_stream_f32(kind, P.R, grid, smem, st, *map, S)
+                                       : launch_stream_bf16(kind, P.R, grid, smem, st, *map, S);
+    count_launch();
+    if (e != cudaSuccess) return cuda_fail(e, "MTTKRP streaming kernel launch");
+    if (timer && timer->stop) NTF_CUDA_TRY(cudaEventRecord(timer->stop, st));
+    return NTF_OK;
+}
+
 ntf_status run_mttkrp(const TensorView& v, const MttkrpPlan& P, const float* const* factors, float* out,
                       void* workspace, cudaStream_t st, TmapCache* cache, StreamTimer* timer) {
     const int N = v.order, r = P.rank, n = P.mode;
@@ -300,27 +339,6 @@ ntf_status run_mttkrp(const TensorView& v, const MttkrpPlan& P, const float* con
     float* Fi = reinterpret_cast<float*>(ws + P.off_Fi);
     float* W = reinterpret_cast<float*>(ws + P.off_W);
     float* part = reinterpret_cast<float*>(ws + P.off_part);
-
-    // tensor map
-    CUtensorMap local_map;
-    const CUtensorMap* map = &local_map;
-    if (cache && cache->valid && cache->data == v.data && cache->I_T == P.I_T && cache->O_T == P.O_T) {
-        map = &cache->map;
-    } else {
-        const uint32_t box0 = 128 / v.es;
-        ntf_status s = encode_tensor_map_3d(&local_map, v.dtype, v.data, (uint64_t)v.C, (uint64_t)v.Ii,
-                                            (uint64_t)v.n_o, (uint64_t)(v.ld * v.es),
-                                            (uint64_t)(v.Ii * v.ld * v.es), box0, (uint32_t)P.I_T, (uint32_t)P.O_T);
-        if (s != NTF_OK) return s;
-        if (cache) {
-            cache->valid = true;
-            cache->data = v.data;
-            cache->I_T = P.I_T;
-            cache->O_T = P.O_T;
-            cache->map = local_map;
-            map = &cache->map;
-        }
-    }
 
     // 1. packed factors and weight table
     if (P.kind != ModeKind::Last) {
@@ -345,73 +363,14 @@ ntf_status run_mttkrp(const TensorView& v, const MttkrpPlan& P, const float* con
     }
 
     // 2. streaming kernel
-    StreamParams S{};
-    S.C = v.C;
-    S.Ii = v.Ii;
-    S.n_o = v.n_o;
-    S.I_T = P.I_T;
-    S.O_T = P.O_T;
-    S.nb = P.nb;
-    S.n_ot = P.n_ot;
-    S.n_tiles = P.n_tiles;
-    S.n_kc = P.n_kc;
-    S.RP = P.RP;
-    S.Smax = P.Smax;
-    S.Cpad = P.Cpad;
-    S.Fc = Fc;
-    S.Fi = Fi;
-    S.W = W;
-    S.part = part;
-    S.err = device_error_word();
-    const int kind = P.kind == ModeKind::Inner ? 0 : P.kind == ModeKind::Outer ? 1 : 2;
-    dim3 grid;
-    size_t smem;
-    if (P.kind == ModeKind::Last) {
-        grid = dim3(P.G, P.n_cb, P.n_pb);
-        smem = stream_last_smem(v.es, P.R);
-    } else {
-        grid = dim3(P.G, P.n_pb, 1);
-        smem = stream_rows_smem(v.es, P.RP);
-    }
-    if (timer && timer->start) NTF_CUDA_TRY(cudaEventRecord(timer->start, st));
-    cudaError_t e = v.dtype == NTF_F32 ? launch_stream_f32(kind, P.R, grid, smem, st, *map, S)
-                                       : launch_stream_bf16(kind, P.R, grid, smem, st, *map, S);
-    count_launch();
-    if (e != cudaSuccess) return cuda_fail(e, "MTTKRP streaming kernel launch");
-    if (timer && timer->stop) NTF_CUDA_TRY(cudaEventRecord(timer->stop, st));
+    ntf_status s = run_mttkrp_stream(v, P, workspace, st, cache, timer);
+    if (s != NTF_OK) return s;
 
     // 3. deterministic reduction into the user's I_n x r output
-    ReduceParams R{};
-    R.n_tiles = P.n_tiles;
-    R.n_ot = P.n_ot;
-    R.nb = P.nb;
-    R.Ii = v.Ii;
-    R.n_o = v.n_o;
-    R.C = v.C;
-    R.Cpad = P.Cpad;
-    R.G = P.G;
-    R.Smax = P.Smax;
-    R.I_T = P.I_T;
-    R.RP = P.RP;
-    R.r = r;
-    R.part = part;
-    R.W = W;
-    R.out = out;
-    if (P.kind == ModeKind::Inner) {
-        k_reduce_inner<<<grid_for(v.Ii * r, 128), 128, 0, st>>>(R);
-        NTF_LAUNCH_CHECK("k_reduce_inner");
-    } else if (P.kind == ModeKind::Outer) {
-        R.In = v.dims[n];
-        int64_t stride = 1;
-        for (int l = n + 1; l < N - 2; ++l) stride *= v.dims[l];
-        R.stride = stride;
-        R.hi_count = v.n_o / (R.In * stride);
-        k_reduce_outer<<<grid_for(R.In * r, 128), 128, 0, st>>>(R);
-        NTF_LAUNCH_CHECK("k_reduce_outer");
-    } else {
-        k_reduce_last<<<grid_for(v.C * r, 128), 128, 0, st>>>(R);
-        NTF_LAUNCH_CHECK("k_reduce_last");
-    }
+    ReduceParams R = make_reduce_params(v, P, part, W);
+    const int64_t n_out = v.dims[n];
+    k_reduce<<<grid_for(n_out * r, 128), 128, 0, st>>>(R, n_out, out);
+    NTF_LAUNCH_CHECK("k_reduce");
     return NTF_OK;
 }
 

@@ -51,7 +51,8 @@ struct TileBytes {
 };
 
 inline size_t stream_rows_smem(int elem_bytes, int RP) {
-    return (size_t)kStreamStages * (kTileRows * kStageCols * elem_bytes + kStageCols * RP * 4) + 1024 + 128;
+    // stages + barriers (128 B) + double-buffered cross-warp sums of the outer mode (2 x 8 x 32 floats)
+    return (size_t)kStreamStages * (kTileRows * kStageCols * elem_bytes + kStageCols * RP * 4) + 1024 + 128 + 2048;
 }
 inline size_t stream_last_smem(int elem_bytes, int R) {
     return (size_t)kStreamStages * (kTileRows * kStageCols * elem_bytes + kTileRows * R * 4) + 1024 + 128;
@@ -86,6 +87,14 @@ __device__ __forceinline__ void tile_range(int64_t n_tiles, int g, int G, int64_
     e = (n_tiles * (g + 1)) / G;
 }
 
+// Bounded wait taken by a whole warp: every lane polls (so every lane gets the
+// barrier's acquire ordering) and the warp agrees on one outcome, so a time-out
+// can never split a warp before a shuffle or a named barrier.
+__device__ __forceinline__ bool warp_wait_bounded(uint64_t* bar, uint32_t parity) {
+    const bool mine = mbar_wait_bounded(bar, parity);
+    return __all_sync(0xffffffffu, mine) != 0;
+}
+
 // Producer drain: wait (bounded) until every copy this thread issued has
 // landed, so that no TMA write is in flight when the CTA retires.
 __device__ __forceinline__ void drain_stages(uint64_t* full, int stage, uint32_t phase, int64_t issued, int* err) {
@@ -113,6 +122,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     unsigned char* fchunk_ptr = base_ptr + kStreamStages * TB::value;
     uint64_t* full = reinterpret_cast<uint64_t*>(fchunk_ptr + kStreamStages * fbytes);
     uint64_t* empty = full + kStreamStages;
+    float* zsum = reinterpret_cast<float*>(fchunk_ptr + kStreamStages * fbytes + 128);   // [2][8][32]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x, G = gridDim.x;
@@ -181,14 +191,18 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     uint32_t phase = 0;
     int64_t cur_ib = -1;
     int seg = 0;
+    int tile_parity = 0;
     bool ok = true;
     const int kw = warp * 8;  // this warp's 8 columns inside a 64-column stage
 
-    for (int64_t t = t_beg; t < t_end && ok; ++t) {
+    // A warp that gives up a bounded wait stops computing and stops arriving on
+    // the ring, but keeps walking the tiles so that it still joins every named
+    // barrier of the outer-mode epilogue: no barrier can hang.
+    for (int64_t t = t_beg; t < t_end; ++t) {
         int64_t ib, ot;
         if (INNER) { ib = t / P.n_ot; ot = t % P.n_ot; }
         else { ot = t / P.nb; ib = t % P.nb; }
-        if (INNER && ib != cur_ib) {
+        if (INNER && ok && ib != cur_ib) {
             if (cur_ib >= 0) {
                 // flush the finished inner block: lanes l, l+I_T, ... share row l % I_T
                 for (int off = P.I_T; off < 32; off <<= 1) {
@@ -210,12 +224,11 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
             cur_ib = ib;
         }
         for (int kc = 0; kc < P.n_kc; ++kc) {
-            if (!mbar_wait_bounded(&full[stage], phase)) {
-                record_device_error(P.err, kErrWaitFull);
+            if (ok && !warp_wait_bounded(&full[stage], phase)) {
+                if (lane == 0) record_device_error(P.err, kErrWaitFull);
                 ok = false;
-                break;
             }
-            if ((int64_t)kc * kStageCols + kw < P.C) {
+            if (ok && (int64_t)kc * kStageCols + kw < P.C) {
                 const uint32_t tb = base + stage * TB::value;
                 const uint32_t fb = fchunk_base + stage * fbytes;
                 if constexpr (sizeof(TE) == 4) {
@@ -275,12 +288,11 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[stage]);
+            if (ok && lane == 0) mbar_arrive(&empty[stage]);
             if (++stage == kStreamStages) { stage = 0; phase ^= 1u; }
         }
-        if (!ok) break;
         // ---------------- tile epilogue ----------------
-        if (INNER) {
+        if (INNER && ok) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int64_t o = ot * P.O_T + (lane + 32 * j) / P.I_T;
@@ -296,7 +308,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                     }
                 }
             }
-        } else {
+        } else if (!INNER) {
             // one outer index per tile (I_T = 128, O_T = 1): z = sum_rows Y(row) A_{N-2}(i(row))
             float z[R];
 #pragma unroll
@@ -325,7 +337,18 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 #pragma unroll
             for (int p = 0; p < R; ++p)
                 if (p == lane) mine = z[p];
-            if (lane < R) P.part[(((ot * P.nb) + ib) * kStreamWarps + warp) * P.RP + p0 + lane] = mine;
+            // sum the 8 warps' column sums in shared memory (buffer alternates by tile parity,
+            // so one barrier per tile suffices) and write one partial per tile
+            float* zs = zsum + (tile_parity * kStreamWarps) * 32;
+            zs[warp * 32 + lane] = mine;
+            named_bar_sync(1, kStreamWarps * 32);
+            if (warp == 0 && lane < R && ok) {
+                float t = 0.f;
+#pragma unroll
+                for (int w = 0; w < kStreamWarps; ++w) t += zs[w * 32 + lane];
+                P.part[((ot * P.nb) + ib) * P.RP + p0 + lane] = t;
+            }
+            tile_parity ^= 1;
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -444,8 +467,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
     int stage = 0;
     uint32_t phase = 0;
     for (int64_t t = t_beg; t < t_end; ++t) {
-        if (!mbar_wait_bounded(&full[stage], phase)) {
-            record_device_error(P.err, kErrWaitFull);
+        if (!warp_wait_bounded(&full[stage], phase)) {
+            if (lane == 0) record_device_error(P.err, kErrWaitFull);
             break;
         }
         if (col_live) {

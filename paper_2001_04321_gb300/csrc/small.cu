@@ -633,6 +633,17 @@ __global__ void k_her_copy(const ntf_her_state* s, CopyPairs P) {
     }
 }
 
+cudaError_t launch_her_copy(const ntf_her_state* s, const CopyPairs& P, cudaStream_t st) {
+    int64_t maxn = P.gn;
+    for (int q = 0; q < P.count; ++q) maxn = P.n[q] > maxn ? P.n[q] : maxn;
+    int64_t g = (maxn + 255) / 256;
+    if (g > 256) g = 256;
+    if (g < 1) g = 1;
+    k_her_copy<<<(int)g, 256, 0, st>>>(s, P);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_her_step(ntf_her_state* s, const double* fhat, const CopyPairs& P, cudaStream_t st) {
     k_her_decide<<<1, 1, 0, st>>>(s, fhat);
     count_launch();

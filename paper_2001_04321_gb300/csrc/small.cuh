@@ -46,6 +46,7 @@ cudaError_t launch_to_bf16(const float* src, int64_t rows, int64_t C, int64_t ld
 cudaError_t launch_her_init(ntf_her_state* s, double beta0, double gamma, double gamma_bar, double eta,
                             const double* f0, cudaStream_t st);
 cudaError_t launch_her_step(ntf_her_state* s, const double* fhat, const CopyPairs& P, cudaStream_t st);
+cudaError_t launch_her_copy(const ntf_her_state* s, const CopyPairs& P, cudaStream_t st);
 
 // W(o,p) for the residual: product over all modes < N-2 (packed width RP)
 cudaError_t launch_weights_all(const TensorView& v, const float* const* factors, int r, int RP, float* W,

@@ -3,6 +3,7 @@
 // of kernels on one stream with no host round trip (the restart decision is
 // taken on the device), so it can also be replayed as a CUDA graph.
 #include "small.cuh"
+#include "epilogue.cuh"
 
 #include <chrono>
 #include <cmath>
@@ -40,6 +41,11 @@ struct Solver {
     bool timing = false;
     std::vector<StreamTimer> ev;
     size_t ev_used = 0;
+    // fused main path (HALS, one sweep, rank <= 32)
+    bool fused = false;
+    float* gpart = nullptr;
+    double* ipart = nullptr;
+    unsigned* ticket = nullptr;
     // graph replay
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
@@ -78,8 +84,82 @@ struct Solver {
         return &ev[ev_used++];
     }
 
+    CopyPairs her_pairs() const {
+        CopyPairs P;
+        P.count = N;
+        P.gcount = N;
+        P.gn = r * r;
+        for (int l = 0; l < N; ++l) {
+            P.a[l] = A[l];
+            P.ah[l] = Ah[l];
+            P.n[l] = vs.dims[l] * r;
+            P.g[l] = G[l];
+            P.gh[l] = Gh[l];
+        }
+        return P;
+    }
+
+    // one outer iteration on the fused path: per mode prep -> stream -> epilogue,
+    // then (HER) the accept/restart copies decided by the last epilogue
+    ntf_status iterate_fused(cudaStream_t st) {
+        const bool use_her = o.her != 0;
+        unsigned char* ws = static_cast<unsigned char*>(ws_mt);
+        for (int n = 0; n < N; ++n) {
+            const MttkrpPlan& P = plan[n];
+            PrepParams pp{};
+            pp.order = N;
+            pp.mode = n;
+            pp.skip = P.kind == ModeKind::Outer ? n : -1;
+            pp.r = r;
+            pp.RP = P.RP;
+            pp.C = vs.C;
+            pp.Ii = vs.Ii;
+            pp.n_o = vs.n_o;
+            pp.Fc_rows_out = round_up(vs.C, 64);
+            for (int l = 0; l < N; ++l) {
+                pp.dims[l] = vs.dims[l];
+                pp.A[l] = Ah[l];
+                pp.Gh[l] = Gh[l];
+            }
+            pp.V = V;
+            pp.Fc = P.kind != ModeKind::Last ? reinterpret_cast<float*>(ws + P.off_Fc) : nullptr;
+            pp.Fi = P.kind != ModeKind::Inner ? reinterpret_cast<float*>(ws + P.off_Fi) : nullptr;
+            pp.W = reinterpret_cast<float*>(ws + P.off_W);
+            cudaError_t e = launch_prep(pp, st);
+            if (e != cudaSuccess) return cuda_fail(e, "prep");
+            ntf_status s = run_mttkrp_stream(vs, P, ws_mt, st, &tm[n], next_timer());
+            if (s != NTF_OK) return s;
+            EpiParams ep{};
+            ep.red = make_reduce_params(vs, P, reinterpret_cast<const float*>(ws + P.off_part),
+                                        reinterpret_cast<const float*>(ws + P.off_W));
+            ep.rows = vs.dims[n];
+            ep.r = r;
+            ep.A = A[n];
+            ep.Ah = use_her ? Ah[n] : nullptr;
+            ep.beta = &her->beta;
+            ep.V = V;
+            ep.gpart = gpart;
+            ep.ipart = ipart;
+            ep.ticket = ticket;
+            ep.G_out = use_her ? G[n] : Gh[n];
+            ep.Gh_out = use_her ? Gh[n] : nullptr;
+            ep.last = n == N - 1 ? 1 : 0;
+            ep.tnorm = &scal[0];
+            ep.fhat_out = &scal[1];
+            ep.her = use_her ? her : nullptr;
+            e = launch_epilogue(ep, st);
+            if (e != cudaSuccess) return cuda_fail(e, "epilogue");
+        }
+        if (use_her) {
+            cudaError_t e = launch_her_copy(her, her_pairs(), st);
+            if (e != cudaSuccess) return cuda_fail(e, "her copy");
+        }
+        return NTF_OK;
+    }
+
     // one outer iteration of Alg. 2 (or Alg. 1 when her == 0)
     ntf_status iterate(cudaStream_t st) {
+        if (fused) return iterate_fused(st);
         const bool use_her = o.her != 0;
         for (int n = 0; n < N; ++n) {
             const int64_t rows = vs.dims[n];
@@ -234,6 +314,14 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     }
     if ((s = S->alloc(&S->ws_mt, ws)) != NTF_OK) return bail(s);
     if ((s = S->alloc(&S->ws_bcd, bcd_workspace(maxrows))) != NTF_OK) return bail(s);
+    S->fused = S->o.method == NTF_HALS && S->o.inner_max == 1 && r <= 32;
+    if (S->fused) {
+        const int64_t blocks = epilogue_blocks(maxrows);
+        if ((s = S->alloc((void**)&S->gpart, sizeof(float) * (size_t)blocks * 2 * r * r)) != NTF_OK) return bail(s);
+        if ((s = S->alloc((void**)&S->ipart, sizeof(double) * (size_t)blocks)) != NTF_OK) return bail(s);
+        if ((s = S->alloc((void**)&S->ticket, 256)) != NTF_OK) return bail(s);
+        NTF_CUDA_TRY(cudaMemsetAsync(S->ticket, 0, 256, st));
+    }
     S->ws_res_bytes = (((sizeof(float) * (size_t)S->vu.n_o * round_up(r, 4)) + 255) & ~size_t(255)) +
                       sizeof(double) * (size_t)std::max(stream_red_blocks(), 1);
     if ((s = S->alloc(&S->ws_res, S->ws_res_bytes)) != NTF_OK) return bail(s);

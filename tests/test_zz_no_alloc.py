@@ -54,7 +54,7 @@ def test_noalloc_matches_workspace_entry_on_two_calls_in_a_row():
 def test_noalloc_rejects_requests_beyond_its_scratch():
     import torch
     import paper_2001_04321_gb300 as ntf
-    dims, r, mode = (8192, 200, 4), 64, 0
+    dims, r, mode = (8, 8192, 4), 64, 1
     T = torch.rand(*dims, device="cuda")
     F = [torch.rand(n, r, device="cuda") for n in dims]
     assert ntf.mttkrp_workspace_bytes(T, r, mode) > (16 << 20)
