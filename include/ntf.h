@@ -308,8 +308,14 @@ NTF_API ntf_status ntf_solve_host(const ntf_tensor* T_host, float* const* factor
 typedef struct ntf_solver ntf_solver;
 NTF_API ntf_status ntf_solver_create(ntf_solver** out, const ntf_tensor* T, float* const* factors, int rank,
                              const ntf_opts* opts, void* stream);
-/* Run `iters` outer iterations on `stream` (asynchronous). */
+/* Run `iters` outer iterations on `stream` (asynchronous).  With opts.use_graph
+ * and a non-default stream, iterations are captured once into CUDA graphs of up
+ * to 1024 iterations and replayed. */
 NTF_API ntf_status ntf_solver_run(ntf_solver* s, int iters, void* stream);
+/* With opts.use_graph: capture `iters` (1..1024) outer iterations into one CUDA
+ * graph now, so that a later ntf_solver_run(s, iters, stream) on the same stream
+ * only replays it.  With timing on, the graph records the MTTKRP events too. */
+NTF_API ntf_status ntf_solver_prepare_graph(ntf_solver* s, int iters, void* stream);
 /* Copy the current factors A_k into `factors` (HOST array of device pointers). */
 NTF_API ntf_status ntf_solver_get_factors(ntf_solver* s, float* const* factors, void* stream);
 /* Synchronise and fill `report` (f_true_last computed explicitly here). */

@@ -97,6 +97,7 @@ _SIGS = {
     "ntf_solver_create": (C.c_int, [C.POINTER(_P), C.POINTER(_Tensor), C.POINTER(_P), C.c_int, C.POINTER(_Opts),
                                     _P]),
     "ntf_solver_run": (C.c_int, [_P, C.c_int, _P]),
+    "ntf_solver_prepare_graph": (C.c_int, [_P, C.c_int, _P]),
     "ntf_solver_get_factors": (C.c_int, [_P, C.POINTER(_P), _P]),
     "ntf_solver_report": (C.c_int, [_P, C.POINTER(_Report), _P]),
     "ntf_solver_set_timing": (C.c_int, [_P, C.c_int]),
@@ -438,6 +439,9 @@ class Solver:
 
     def run(self, iters: int, stream=None):
         _check(load().ntf_solver_run(self._h, int(iters), _stream(stream)))
+
+    def prepare_graph(self, iters: int, stream=None):
+        _check(load().ntf_solver_prepare_graph(self._h, int(iters), _stream(stream)))
 
     def get_factors(self, factors: List, stream=None):
         _check(load().ntf_solver_get_factors(self._h, _ptr_array(factors), _stream(stream)))

@@ -1,24 +1,33 @@
 // Fused per-mode kernels of the solver's main path (HALS with one sweep per
-// block update, rank <= 32):
+// block update, rank <= 32).  Per mode n:
 //
-//   k_prep      V_n = Hadamard product of the Grams of A_hat_l, l != n (Appendix A),
-//               packed factors and the weight table W for the MTTKRP stream;
+//   k_prep      finishes the Grams of the mode updated just before (FP64 sums
+//               of the epilogue's per-CTA partials; at mode 0 the last mode of
+//               the previous iteration, kept or discarded by its restart
+//               decision), forms V_n = Hadamard product of the Grams of the
+//               pairing factors A_hat_l, l != n (Appendix A), and packs the
+//               factors and the weight table W for the MTTKRP stream;
 //   k_epilogue  per row j of mode n: M(j,:) from the stream's partial sums (a1),
 //               one HALS sweep (Sec. 2.1.4, Gauss-Seidel over columns), the HER
-//               extrapolation (Alg. 2, eq. extproj_her), per-CTA partial Grams of
-//               A and A_hat (a2); the last CTA to finish (atomic ticket, no
-//               waiting) sums the Grams in FP64 and, for the last mode, forms
-//               F_hat = ||T||^2 - 2<M,A> + sum(V (*) A^T A) (Sec. 3.1, a5) and
-//               takes the restart decision of Alg. 2 (a6).
+//               extrapolation (Alg. 2, eq. extproj_her), and per-CTA partials of
+//               the Grams of A and A_hat, of <M, A> and (last mode) of
+//               sum(V (*) A^T A);
 //
-// One warp owns rows: lane p holds column p of the row, so the HALS column
-// update is a warp-wide dot product.  Every sum has a fixed order.
+// and once per iteration
+//
+//   k_finish    F_hat = ||T||^2 - 2<M,A> + sum(V (*) A^T A) from those partials
+//               (Sec. 3.1, a5), the restart decision of Alg. 2 (a6), and the
+//               accept/restart step as a flip of the current-buffer indices.
+//
+// The HALS sweep keeps the residual g = M - A V of the row in the lanes (lane
+// p holds column p): updating column j is one scalar step on lane j followed
+// by one broadcast and one FMA per lane.  Every sum has a fixed order.
 #include "epilogue.cuh"
 
 namespace ntf {
 
 constexpr int kEpiWarps = 8;
-constexpr int kEpiRowsPerWarp = 4;
+constexpr int kEpiRowsPerWarp = 2;
 constexpr int kEpiRows = kEpiWarps * kEpiRowsPerWarp;   // rows per CTA
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -33,37 +42,116 @@ __device__ __forceinline__ double warp_sum_dd(double v) {
     return v;
 }
 
+// FP64 sum of the epilogue CTAs' FP32 partial Gram entry q (k = 0: A, 1: A_hat), in
+// groups of eight independent loads added as a tree (fixed order)
+__device__ __forceinline__ double sum_gram_partials(const float* gpart, int nblk, int rr, int k, int q) {
+    double s = 0.0;
+    const float* base = gpart + (int64_t)k * rr + q;
+    const int64_t stride = 2 * (int64_t)rr;
+    int b = 0;
+    for (; b + 8 <= nblk; b += 8) {
+        float x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = base[(b + u) * stride];
+        s += (((double)x[0] + x[1]) + ((double)x[2] + x[3])) + (((double)x[4] + x[5]) + ((double)x[6] + x[7]));
+    }
+    for (; b < nblk; ++b) s += (double)base[b * stride];
+    return s;
+}
+
+// pairing factor A_hat_l as seen by the update of mode n (eq. NNLS_her_exact):
+// modes already updated in this iteration use their extrapolated buffer
+__device__ __forceinline__ const float* pairing_factor(const FusedBufs& B, int l, int n) {
+    const int c = B.cur[l];
+    return (B.her && l < n) ? B.X[l][1 - c] : B.X[l][c];
+}
+__device__ __forceinline__ const double* pairing_gram(const FusedBufs& B, int l, int n) {
+    const int c = B.cur[l];
+    return (B.her && l < n) ? B.GB[l][1 - c] : B.GB[l][c];
+}
+
 // ---------------------------------------------------------------------------
 // prep
 // ---------------------------------------------------------------------------
 __global__ void k_prep(const PrepParams P) {
-    const int64_t nV = P.V ? (int64_t)P.r * P.r : 0;
-    const int64_t nFc = P.Fc ? P.Fc_rows_out * P.RP : 0;
+    const int rr = P.r * P.r;
+    const int n = P.mode;
+    const FusedBufs& B = P.B;
+    // Gram finishing for fin_mode; at mode 0 only once an iteration has completed
+    const bool end_of_iter = n == 0;
+    const bool fin = P.fin_mode >= 0 && (!end_of_iter || *B.iters > 0);
+    const bool two = fin && !end_of_iter && B.her;     // mid-iteration with HER: Grams of A and A_hat
+    const int nVG = rr * (two ? 2 : 1);
+    // (1) V and the finished Grams: items spread over the blocks
+    for (int i = blockIdx.x + gridDim.x * threadIdx.x; i < nVG; i += gridDim.x * blockDim.x) {
+        const int q = i % rr;
+        if (i >= rr) {
+            // Gram of A_{n-1} (not extrapolated): only stored
+            const int f = P.fin_mode, c = B.cur[f];
+            B.GB[f][c][q] = sum_gram_partials(P.gpart, P.fin_blocks, rr, 0, q);
+            continue;
+        }
+        double v = 1.0;
+        for (int l = 0; l < P.order; ++l) {
+            if (l == n) continue;
+            double gl;
+            if (fin && l == P.fin_mode) {
+                const int c = B.cur[l];
+                if (end_of_iter) {
+                    // previous iteration's last mode: the kept factor (A on restart, A_hat on accept)
+                    const int k = (B.her && P.her && P.her->last_restart == 0) ? 1 : 0;
+                    gl = sum_gram_partials(P.gpart, P.fin_blocks, rr, k, q);
+                    B.GB[l][c][q] = gl;
+                } else if (B.her) {
+                    gl = sum_gram_partials(P.gpart, P.fin_blocks, rr, 1, q);   // A_hat_{n-1}
+                    B.GB[l][1 - c][q] = gl;
+                } else {
+                    gl = sum_gram_partials(P.gpart, P.fin_blocks, rr, 0, q);
+                    B.GB[l][c][q] = gl;
+                }
+            } else {
+                gl = pairing_gram(B, l, n)[q];
+            }
+            v *= gl;
+        }
+        P.V[q] = v;
+    }
+    // (2) packed factors and weights
+    const int64_t nFc = P.Fc ? P.Fc_rows_out * P.RP : P.FcT ? (int64_t)P.n_kc * 2 * P.RPH * 64 : 0;
     const int64_t nFi = P.Fi ? P.Ii * P.RP : 0;
     const int64_t nW = P.W ? P.n_o * P.RP : 0;
-    const int64_t total = nV + nFc + nFi + nW;
+    const int64_t total = nFc + nFi + nW;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         int64_t k = idx;
-        if (k < nV) {
-            double v = 1.0;
-            for (int l = 0; l < P.order; ++l)
-                if (l != P.mode) v *= P.Gh[l][k];
-            P.V[k] = v;
-            continue;
-        }
-        k -= nV;
         if (k < nFc) {
-            const int64_t i = k / P.RP;
-            const int p = (int)(k % P.RP);
-            P.Fc[k] = (i < P.C && p < P.r) ? P.A[P.order - 1][i * P.r + p] : 0.f;
+            if (P.Fc) {
+                const float* src = pairing_factor(B, P.order - 1, n);
+                const int64_t i = k / P.RP;
+                const int p = (int)(k % P.RP);
+                P.Fc[k] = (i < P.C && p < P.r) ? src[i * P.r + p] : 0.f;
+            } else {
+                // tensor-core B operand: bf16 hi | lo columns, 128-byte rows, swizzled like a TMA box
+                const float* src = pairing_factor(B, P.fct_mode, n);
+                const int N = 2 * P.RPH;
+                const int kl = (int)(k % 64);
+                const int nn = (int)((k / 64) % N);
+                const int64_t kc = k / (64 * (int64_t)N);
+                const int64_t i = kc * 64 + kl;
+                const int p = nn < P.RPH ? nn : nn - P.RPH;
+                const float x = (i < P.fct_rows && p < P.r) ? src[i * P.r + p] : 0.f;
+                const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+                const __nv_bfloat16 v = nn < P.RPH ? hi : __float2bfloat16_rn(x - __bfloat162float(hi));
+                P.FcT[((kc * N + nn) * 128 + (((kl >> 3) ^ (nn & 7)) << 4) + (kl & 7) * 2) / 2] = v;
+            }
             continue;
         }
         k -= nFc;
         if (k < nFi) {
+            const float* src = pairing_factor(B, P.order - 2, n);
             const int64_t i = k / P.RP;
             const int p = (int)(k % P.RP);
-            P.Fi[k] = p < P.r ? P.A[P.order - 2][i * P.r + p] : 0.f;
+            P.Fi[k] = p < P.r ? src[i * P.r + p] : 0.f;
             continue;
         }
         k -= nFi;
@@ -77,7 +165,7 @@ __global__ void k_prep(const PrepParams P) {
                 for (int l = P.order - 3; l >= 0; --l) {
                     const int64_t il = rem % P.dims[l];
                     rem /= P.dims[l];
-                    if (l != P.skip) w *= P.A[l][il * P.r + p];
+                    if (l != P.skip) w *= pairing_factor(B, l, n)[il * P.r + p];
                 }
             }
             P.W[k] = w;
@@ -86,11 +174,12 @@ __global__ void k_prep(const PrepParams P) {
 }
 
 cudaError_t launch_prep(const PrepParams& P, cudaStream_t st) {
-    const int64_t total = (P.V ? (int64_t)P.r * P.r : 0) + (P.Fc ? P.Fc_rows_out * P.RP : 0) +
+    const int64_t total = (int64_t)2 * P.r * P.r +
+                          (P.Fc ? P.Fc_rows_out * P.RP : P.FcT ? (int64_t)P.n_kc * 2 * P.RPH * 64 : 0) +
                           (P.Fi ? P.Ii * P.RP : 0) + (P.W ? P.n_o * P.RP : 0);
     int64_t g = (total + 255) / 256;
     if (g > 2 * num_sms()) g = 2 * num_sms();
-    if (g < 1) g = 1;
+    if (g < 8) g = 8;
     k_prep<<<(int)g, 256, 0, st>>>(P);
     count_launch();
     return cudaGetLastError();
@@ -100,48 +189,66 @@ cudaError_t launch_prep(const PrepParams& P, cudaStream_t st) {
 // epilogue
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) {
-    __shared__ float Vs[32 * 32];
+    __shared__ float Vs[32 * 33];
+    __shared__ float rinv[32];
     __shared__ float rowsA[kEpiRows][32];
     __shared__ float rowsH[kEpiRows][32];
     __shared__ float winner[kEpiWarps];
-    __shared__ double sred[kEpiWarps];
-    __shared__ int is_last;
+    __shared__ double dred[kEpiWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = P.r;
-    const bool her = P.Ah != nullptr;
+    const int r = P.r, n = P.mode;
+    const bool her = P.B.her != 0;
+    const int cn = P.B.cur[n];
+    float* A = P.B.X[n][cn];                      // in: A_{k-1}, out: A_k
+    float* Ah = her ? P.B.X[n][1 - cn] : nullptr; // out: A_hat_k
     for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
         const int l = q >> 5, c = q & 31;
-        Vs[q] = (l < r && c < r) ? (float)P.V[l * r + c] : 0.f;
+        Vs[l * 33 + c] = (l < r && c < r) ? (float)P.V[l * r + c] : 0.f;
     }
     const float beta = her ? (float)*P.beta : 0.f;
 
-    // M rows from the stream's partial sums (independent loads, issued up front)
+    // M rows from the stream's partial sums, and the previous rows
     int64_t row[kEpiRowsPerWarp];
     float m[kEpiRowsPerWarp], a[kEpiRowsPerWarp], a_old[kEpiRowsPerWarp];
 #pragma unroll
     for (int k = 0; k < kEpiRowsPerWarp; ++k) {
         row[k] = (int64_t)blockIdx.x * kEpiRows + warp * kEpiRowsPerWarp + k;
         const bool live = row[k] < P.rows && lane < r;
+        a_old[k] = live ? A[row[k] * r + lane] : 0.f;
         m[k] = live ? reduce_output(P.red, row[k], lane) : 0.f;
-        a_old[k] = live ? P.A[row[k] * r + lane] : 0.f;
         a[k] = a_old[k];
     }
     __syncthreads();
+    if (threadIdx.x < 32) {
+        const float d = Vs[threadIdx.x * 33 + threadIdx.x];
+        rinv[threadIdx.x] = (threadIdx.x < r && d > 0.f) ? 1.f / d : 0.f;
+    }
+    __syncthreads();
 
-    // one HALS sweep per row: a_j <- max(0, M_j - sum_{l != j} a_l V_lj) / V_jj, j = 0..r-1
+    // residual g_p = M_p - sum_l a_l V(l,p), lane p
+    float g[kEpiRowsPerWarp];
+#pragma unroll
+    for (int k = 0; k < kEpiRowsPerWarp; ++k) g[k] = m[k];
+    for (int l = 0; l < r; ++l) {
+        const float vlp = Vs[l * 33 + lane];
+#pragma unroll
+        for (int k = 0; k < kEpiRowsPerWarp; ++k) g[k] = fmaf(-__shfl_sync(0xffffffffu, a[k], l), vlp, g[k]);
+    }
+    // one HALS sweep: a_j <- max(0, M_j - sum_{l != j} a_l V_lj) / V_jj = max(0, g_j + a_j V_jj) / V_jj
     for (int jj = 0; jj < r; ++jj) {
-        const float vlj = Vs[lane * 32 + jj];
-        const float vjj = Vs[jj * 32 + jj];
-        float t[kEpiRowsPerWarp];
+        const float vjj = Vs[jj * 33 + jj];
+        const float rj = rinv[jj];
+        const float vjp = Vs[jj * 33 + lane];
 #pragma unroll
-        for (int k = 0; k < kEpiRowsPerWarp; ++k) t[k] = lane != jj ? a[k] * vlj : 0.f;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int k = 0; k < kEpiRowsPerWarp; ++k) t[k] += __shfl_xor_sync(0xffffffffu, t[k], off);
-        if (lane == jj && vjj > 0.f) {
-#pragma unroll
-            for (int k = 0; k < kEpiRowsPerWarp; ++k) a[k] = fmaxf(m[k] - t[k], 0.f) / vjj;
+        for (int k = 0; k < kEpiRowsPerWarp; ++k) {
+            float delta = 0.f;
+            if (lane == jj && rj > 0.f) {
+                const float nv = fmaxf(fmaf(a[k], vjj, g[k]), 0.f) * rj;
+                delta = nv - a[k];
+                a[k] = nv;
+            }
+            delta = __shfl_sync(0xffffffffu, delta, jj);
+            g[k] = fmaf(-delta, vjp, g[k]);
         }
     }
 
@@ -151,10 +258,10 @@ __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) 
         const bool live = row[k] < P.rows && lane < r;
         float ah = a[k];
         if (live) {
-            P.A[row[k] * r + lane] = a[k];
+            A[row[k] * r + lane] = a[k];
             if (her) {
                 ah = fmaxf(fmaf(beta, a[k] - a_old[k], a[k]), 0.f);
-                P.Ah[row[k] * r + lane] = ah;
+                Ah[row[k] * r + lane] = ah;
             }
             inner = fmaf(m[k], a[k], inner);
         }
@@ -165,82 +272,98 @@ __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) 
     if (lane == 0) winner[warp] = inner;
     __syncthreads();
 
-    // per-CTA partial Grams (FP32 over this CTA's rows)
+    // per-CTA partial Grams (FP32 over this CTA's rows), <M, A>, and sum(V (*) G_cta)
     const int rr = r * r;
+    double quad = 0.0;
     for (int q = threadIdx.x; q < rr; q += blockDim.x) {
         const int p = q / r, c = q % r;
         float sa = 0.f, sh = 0.f;
-#pragma unroll 8
+#pragma unroll
         for (int i = 0; i < kEpiRows; ++i) {
             sa = fmaf(rowsA[i][p], rowsA[i][c], sa);
             sh = fmaf(rowsH[i][p], rowsH[i][c], sh);
         }
         P.gpart[((int64_t)blockIdx.x * 2 + 0) * rr + q] = sa;
         if (her) P.gpart[((int64_t)blockIdx.x * 2 + 1) * rr + q] = sh;
-    }
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < kEpiWarps; ++w) s += (double)winner[w];
-        P.ipart[blockIdx.x] = s;
-    }
-    // the last CTA to arrive finishes the mode (classic fence + ticket; nobody waits)
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(P.ticket, 1u) == gridDim.x - 1) ? 1 : 0;
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-
-    const int nblk = gridDim.x;
-    double quad = 0.0;
-    for (int q = threadIdx.x; q < rr; q += blockDim.x) {
-        double ga = 0.0, gh = 0.0;
-        for (int b = 0; b < nblk; ++b) {
-            ga += (double)P.gpart[((int64_t)b * 2 + 0) * rr + q];
-            if (her) gh += (double)P.gpart[((int64_t)b * 2 + 1) * rr + q];
-        }
-        P.G_out[q] = ga;
-        if (her) P.Gh_out[q] = gh;
-        quad += P.V[q] * ga;
+        if (P.last) quad += P.V[q] * (double)sa;
     }
     if (P.last) {
         quad = warp_sum_dd(quad);
-        if (lane == 0) sred[warp] = quad;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double qsum = 0.0, isum = 0.0;
-            for (int w = 0; w < kEpiWarps; ++w) qsum += sred[w];
-            for (int b = 0; b < nblk; ++b) isum += P.ipart[b];
-            const double fhat = *P.tnorm - 2.0 * isum + qsum;
-            *P.fhat_out = fhat;
-            if (her) {
-                // Alg. 2: restart if F_hat_k > F_hat_{k-1}; a non-finite F_hat restarts and is flagged
-                ntf_her_state* s = P.her;
-                const double b0 = s->beta, bb = s->beta_bar;
-                const bool finite = isfinite(fhat);
-                const bool restart = !finite || fhat > s->f_hat_prev;
-                if (restart) {
-                    s->beta_bar = b0;
-                    s->beta = b0 / s->eta;
-                } else {
-                    s->beta_bar = fmin(1.0, s->gamma_bar * bb);
-                    s->beta = fmin(bb, s->gamma * b0);
-                }
-                s->f_hat_prev = fhat;
-                s->iters += 1;
-                s->restarts += restart ? 1 : 0;
-                s->last_restart = restart ? 1 : 0;
-                if (!finite) s->numeric_error = 1;
-            }
+        if (lane == 0) dred[warp] = quad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0, qs = 0.0;
+        for (int w = 0; w < kEpiWarps; ++w) s += (double)winner[w];
+        P.ipart[blockIdx.x] = s;
+        if (P.last) {
+            for (int w = 0; w < kEpiWarps; ++w) qs += dred[w];
+            P.qpart[blockIdx.x] = qs;
         }
     }
-    if (threadIdx.x == 0) *P.ticket = 0u;
 }
 
 int epilogue_blocks(int64_t rows) { return (int)((rows + kEpiRows - 1) / kEpiRows); }
 
 cudaError_t launch_epilogue(const EpiParams& P, cudaStream_t st) {
     k_epilogue<<<epilogue_blocks(P.rows), kEpiWarps * 32, 0, st>>>(P);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// end of an iteration: F_hat, the restart decision, the buffer flip
+// ---------------------------------------------------------------------------
+constexpr int kFinishThreads = 256;
+
+__global__ void __launch_bounds__(kFinishThreads) k_finish(const FinishParams P) {
+    __shared__ double sred[2][kFinishThreads / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double inner = 0.0, quad = 0.0;
+    for (int b = threadIdx.x; b < P.blocks; b += blockDim.x) {
+        inner += P.ipart[b];
+        quad += P.qpart[b];
+    }
+    inner = warp_sum_dd(inner);
+    quad = warp_sum_dd(quad);
+    if (lane == 0) {
+        sred[0][warp] = inner;
+        sred[1][warp] = quad;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double isum = 0.0, qsum = 0.0;
+    for (int w = 0; w < kFinishThreads / 32; ++w) {
+        isum += sred[0][w];
+        qsum += sred[1][w];
+    }
+    const double fhat = *P.tnorm - 2.0 * isum + qsum;
+    *P.fhat_out = fhat;
+    *P.iters_out += 1;
+    if (!P.her) return;
+    // Alg. 2: restart if F_hat_k > F_hat_{k-1}; a non-finite F_hat restarts and is flagged
+    ntf_her_state* s = P.her;
+    const double b0 = s->beta, bb = s->beta_bar;
+    const bool finite = isfinite(fhat);
+    const int restart = (!finite || fhat > s->f_hat_prev) ? 1 : 0;
+    if (restart) {
+        s->beta_bar = b0;
+        s->beta = b0 / s->eta;
+    } else {
+        s->beta_bar = fmin(1.0, s->gamma_bar * bb);
+        s->beta = fmin(bb, s->gamma * b0);
+        // keep the extrapolated sequence: A_k <- A_hat_k for every block
+        for (int l = 0; l < P.order; ++l) P.B.cur[l] = 1 - P.B.cur[l];
+    }
+    s->f_hat_prev = fhat;
+    s->iters += 1;
+    s->restarts += restart;
+    s->last_restart = restart;
+    if (!finite) s->numeric_error = 1;
+}
+
+cudaError_t launch_finish(const FinishParams& P, cudaStream_t st) {
+    k_finish<<<1, kFinishThreads, 0, st>>>(P);
     count_launch();
     return cudaGetLastError();
 }

@@ -1,43 +1,72 @@
-// Fused prep / epilogue kernels of the solver's main path (see epilogue.cu).
+// Fused prep / epilogue / finish kernels of the solver's main path (see epilogue.cu).
 #pragma once
 
 #include "mttkrp.cuh"
+#include "small.cuh"
 
 namespace ntf {
 
+// Two buffers per mode for the factor and its Gram.  At the start of every
+// iteration A_l and A_hat_l are equal (Alg. 2 sets one to the other) and live
+// in X[l][cur[l]]; during the iteration mode l's update writes A_l there and
+// A_hat_l to X[l][1 - cur[l]] (with HER).  Accepting the extrapolation flips
+// cur[l]; restarting keeps it.  No factor is ever copied.
+struct FusedBufs {
+    float* X[NTF_MAX_ORDER][2];
+    double* GB[NTF_MAX_ORDER][2];   // Gram of the factor in X[l][k]
+    int* cur;                       // device: current buffer of each mode
+    const int* iters;               // device: outer iterations completed (decisions taken)
+    int her;
+};
+
 struct PrepParams {
+    FusedBufs B;
     int order, mode, skip, r, RP;
     int64_t C, Ii, n_o, Fc_rows_out;
     int64_t dims[NTF_MAX_ORDER];
-    const float* A[NTF_MAX_ORDER];     // factors entering the MTTKRP (the pairing A_hat)
-    const double* Gh[NTF_MAX_ORDER];   // their Grams
-    double* V;                          // r x r, or nullptr
-    float* Fc;                          // packed last-mode factor, or nullptr
-    float* Fi;                          // packed second-to-last factor, or nullptr
-    float* W;                           // weight table, or nullptr
+    double* V;                          // r x r
+    float* Fc;                          // packed last-mode factor (FFMA stream), or nullptr
+    __nv_bfloat16* FcT;                 // tensor-core operand (64-row chunks, bf16 hi|lo), or nullptr
+    int fct_mode;                       // mode packed into FcT
+    int64_t fct_rows;                   // its rows
+    int RPH, n_kc;                      // n_kc: 64-row chunks of FcT
+    float* Fi;                          // packed second-to-last factor (FFMA stream), or nullptr
+    float* W;                           // weight table
+    // Grams of the mode updated just before (fin_mode) are finished here from the
+    // epilogue partials; for mode 0 that is the last mode of the previous iteration
+    int fin_mode, fin_blocks;
+    const float* gpart;                 // [blocks][2][r*r]
+    const ntf_her_state* her;           // decision of the previous iteration (mode-0 prep), or nullptr
 };
 
 struct EpiParams {
+    FusedBufs B;
     ReduceParams red;
+    int mode;
     int64_t rows;
     int r;
-    float* A;              // in: A_{k-1}^n, out: A_k^n
-    float* Ah;             // out: A_hat_k^n (nullptr without HER)
+    int last;              // 1 for mode N-1: also partial sum(V (*) G(A))
     const double* beta;    // device beta_{k-1}
     const double* V;       // r x r
-    float* gpart;          // [blocks][2][r*r]
-    double* ipart;         // [blocks]
-    unsigned* ticket;      // zero between launches
-    double* G_out;         // Gram of A_k^n
-    double* Gh_out;        // Gram of A_hat_k^n (nullptr without HER)
-    int last;              // 1 for mode N-1: objective and restart decision
+    float* gpart;          // [blocks][2][r*r]: partial Grams of A and A_hat
+    double* ipart;         // [blocks]: partial <M, A>
+    double* qpart;         // [blocks]: partial sum(V (*) G(A)) (last mode)
+};
+
+struct FinishParams {
+    FusedBufs B;
+    int order, blocks;     // blocks: epilogue CTAs of the last mode
+    const double* ipart;
+    const double* qpart;
     const double* tnorm;
     double* fhat_out;
+    int* iters_out;        // outer-iteration counter
     ntf_her_state* her;    // nullptr without HER
 };
 
 cudaError_t launch_prep(const PrepParams& P, cudaStream_t st);
 cudaError_t launch_epilogue(const EpiParams& P, cudaStream_t st);
+cudaError_t launch_finish(const FinishParams& P, cudaStream_t st);
 int epilogue_blocks(int64_t rows);
 
 // streaming kernel of a plan alone (the packed factors / W already in place)

@@ -26,6 +26,8 @@ enum class ModeKind { Inner, Outer, Last };
 
 struct MttkrpPlan {
     ModeKind kind;
+    bool tc;             // tcgen05 kernels (bf16 storage, rank <= 32)
+    int RPH;             // tc: rank rounded up to 8 (B operand holds hi | lo, N = 2 RPH)
     int mode, rank, RP, R, n_pb;
     int I_T, O_T;
     int64_t nb, n_ot, n_tiles;
@@ -35,7 +37,7 @@ struct MttkrpPlan {
     int Smax;
     int64_t Cpad;
     // workspace layout (byte offsets)
-    size_t off_Fc, off_Fi, off_W, off_part, total;
+    size_t off_Fc, off_Fi, off_W, off_part, total;   // off_Fc holds FcT (bf16) on the tc path
 };
 
 ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* plan);

@@ -5,6 +5,7 @@
 #include "mttkrp_kernels.cuh"
 #include "mttkrp_reduce.cuh"
 #include "epilogue.cuh"
+#include "mttkrp_tc.cuh"
 
 #include <cmath>
 #include <cstring>
@@ -99,10 +100,13 @@ ntf_status encode_tensor_map_3d(CUtensorMap* map, ntf_dtype dtype, const void* b
 // ---------------------------------------------------------------------------
 static double util(int64_t n, int64_t t) { return (double)n / (double)(t * ceil_div(n, t)); }
 
-// tile shape (I_T inner x O_T outer, I_T * O_T = 128) with the fewest padded rows
-static void choose_tile(int64_t Ii, int64_t n_o, int max_IT, int* I_T, int* O_T) {
+// tile shape (I_T inner x O_T outer, I_T * O_T = 128) with the fewest padded rows;
+// on ties the inner mode prefers the smallest I_T (fewer streaming CTAs share an
+// inner block, so its reduction sums fewer partials), the last mode the largest
+static void choose_tile(int64_t Ii, int64_t n_o, int max_IT, bool prefer_small, int* I_T, int* O_T) {
     double best = -1;
-    for (int it = max_IT; it >= 1; it >>= 1) {
+    for (int k = 0; (1 << k) <= max_IT; ++k) {
+        const int it = prefer_small ? (1 << k) : (max_IT >> k);
         const int ot = 128 / it;
         const double u = util(Ii, it) * util(n_o, ot);
         if (u > best + 1e-9) { best = u; *I_T = it; *O_T = ot; }
@@ -119,31 +123,35 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     P.rank = rank;
     if (rank <= 32) {
         P.RP = (int)round_up(rank, 4);
-        if (P.RP == 28) P.RP = 32;    // kernels are instantiated for 4..24 and 32 columns
+        if (P.RP == 28) P.RP = 32;    // FFMA kernels are instantiated for 4..24 and 32 columns
         P.R = P.RP;
     } else {
         P.RP = 64;
         P.R = 32;
     }
     P.n_pb = P.RP / P.R;
+    P.tc = v.dtype == NTF_BF16 && rank <= 32;
+    P.RPH = (int)round_up(rank, 8);
     P.kind = mode == v.order - 1 ? ModeKind::Last : mode == v.order - 2 ? ModeKind::Inner : ModeKind::Outer;
-    if (P.kind == ModeKind::Inner) choose_tile(v.Ii, v.n_o, 32, &P.I_T, &P.O_T);
-    else if (P.kind == ModeKind::Outer) { P.I_T = 128; P.O_T = 1; }
-    else choose_tile(v.Ii, v.n_o, 128, &P.I_T, &P.O_T);
+    if (P.kind == ModeKind::Inner) choose_tile(v.Ii, v.n_o, 32, false, &P.I_T, &P.O_T);
+    else if (P.kind == ModeKind::Outer || P.tc) { P.I_T = 128; P.O_T = 1; }   // tc last mode: W(o,:) per tile
+    else choose_tile(v.Ii, v.n_o, 128, false, &P.I_T, &P.O_T);
     P.nb = ceil_div(v.Ii, P.I_T);
     P.n_ot = ceil_div(v.n_o, P.O_T);
     P.n_tiles = P.nb * P.n_ot;
     P.n_kc = (int)ceil_div(v.C, kStageCols);
     const int sms = num_sms();
-    P.n_cb = (int)ceil_div(v.C, kStageCols);
-    P.Cpad = (int64_t)P.n_cb * kStageCols;
+    const int cb_cols = P.tc ? 128 : kStageCols;
+    P.n_cb = (int)ceil_div(v.C, cb_cols);
+    P.Cpad = (int64_t)P.n_cb * cb_cols;
     if (P.kind == ModeKind::Last) {
         int gs = sms / P.n_cb;
         if (gs < 1) gs = 1;
         if (gs > P.n_tiles) gs = (int)P.n_tiles;
         P.G = gs;
     } else {
-        P.G = (int)std::min<int64_t>(P.n_tiles, sms);
+        const int per_sm = (P.tc && 2 * tc_rows_smem(P.RPH) <= 227 * 1024) ? 2 : 1;
+        P.G = (int)std::min<int64_t>(P.n_tiles, (int64_t)sms * per_sm);
     }
     P.Smax = 1;
     if (P.kind == ModeKind::Inner) {
@@ -157,7 +165,12 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     }
     size_t off = 0;
     P.off_Fc = off;
-    off = align256(off + sizeof(float) * (size_t)round_up(v.C, kStageCols) * P.RP);
+    if (P.tc && P.kind == ModeKind::Last)
+        off = align256(off + (size_t)P.nb * tc_last_b_bytes(P.RPH));     // packed A_{N-2} blocks
+    else if (P.tc)
+        off = align256(off + (size_t)P.n_kc * (2 * P.RPH) * 128);       // packed A_{N-1} chunks
+    else
+        off = align256(off + sizeof(float) * (size_t)round_up(v.C, kStageCols) * P.RP);
     P.off_Fi = off;
     off = align256(off + sizeof(float) * (size_t)v.Ii * P.RP);
     P.off_W = off;
@@ -165,7 +178,7 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     P.off_part = off;
     size_t part = 0;
     if (P.kind == ModeKind::Inner)
-        part = (size_t)P.G * P.Smax * kStreamWarps * P.I_T * P.RP;
+        part = (size_t)P.G * P.Smax * (P.tc ? 1 : kStreamWarps) * P.I_T * P.RP;
     else if (P.kind == ModeKind::Outer)
         part = (size_t)v.n_o * P.nb * P.RP;
     else
@@ -195,6 +208,29 @@ __global__ void k_pack(const float* __restrict__ A, int64_t rows, int r, int RP,
         const int64_t i = idx / RP;
         const int p = (int)(idx % RP);
         out[idx] = (i < rows && p < r) ? A[i * r + p] : 0.f;
+    }
+}
+
+// Tensor-core B operand of the rows kernel: for every 64-row chunk kc of A_{N-1},
+// N = 2*RPH rows of 128 bytes holding [k = 0..63] of column n as bfloat16, high
+// parts (n < RPH) then low parts (x - hi), 16-byte chunks XOR-swizzled by (n & 7)
+// exactly as a 128-byte-swizzled TMA box would hold them in shared memory.
+__global__ void k_pack_fct(const float* __restrict__ A, int64_t rows, int r, int RPH, int n_kc,
+                           __nv_bfloat16* __restrict__ out) {
+    const int N = 2 * RPH;
+    const int64_t total = (int64_t)n_kc * N * 64;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int kl = (int)(idx % 64);
+        const int n = (int)((idx / 64) % N);
+        const int64_t kc = idx / (64 * (int64_t)N);
+        const int64_t k = kc * 64 + kl;
+        const int p = n < RPH ? n : n - RPH;
+        const float x = (k < rows && p < r) ? A[k * r + p] : 0.f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        const __nv_bfloat16 v = n < RPH ? hi : __float2bfloat16_rn(x - __bfloat162float(hi));
+        const int64_t byte = (kc * N + n) * 128 + (((kl >> 3) ^ (n & 7)) << 4) + (kl & 7) * 2;
+        out[byte / 2] = v;
     }
 }
 
@@ -249,6 +285,7 @@ ReduceParams make_reduce_params(const TensorView& v, const MttkrpPlan& P, const 
     R.I_T = P.I_T;
     R.RP = P.RP;
     R.r = P.rank;
+    R.part_warps = P.tc ? 1 : kStreamWarps;
     R.part = part;
     R.W = W;
     if (P.kind == ModeKind::Outer) {
@@ -264,6 +301,16 @@ ReduceParams make_reduce_params(const TensorView& v, const MttkrpPlan& P, const 
 // ---------------------------------------------------------------------------
 // launch sequence
 // ---------------------------------------------------------------------------
+// Inside a stream capture an event record has to be an external node to
+// record anything when the graph runs; outside a capture a plain record.
+static cudaError_t record_timer_event(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, st);
+}
+
 static ntf_status get_tensor_map(const TensorView& v, const MttkrpPlan& P, TmapCache* cache, CUtensorMap* local,
                                  const CUtensorMap** map) {
     if (cache && cache->valid && cache->data == v.data && cache->I_T == P.I_T && cache->O_T == P.O_T) {
@@ -315,19 +362,46 @@ ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* wor
     const int kind = P.kind == ModeKind::Inner ? 0 : P.kind == ModeKind::Outer ? 1 : 2;
     dim3 grid;
     size_t smem;
-    if (P.kind == ModeKind::Last) {
-        grid = dim3(P.G, P.n_cb, P.n_pb);
-        smem = stream_last_smem(v.es, P.R);
+    cudaError_t e;
+    if (P.tc) {
+        TcParams T{};
+        T.C = v.C;
+        T.Ii = v.Ii;
+        T.n_o = v.n_o;
+        T.I_T = P.I_T;
+        T.O_T = P.O_T;
+        T.nb = P.nb;
+        T.n_ot = P.n_ot;
+        T.n_tiles = P.n_tiles;
+        T.n_kc = P.n_kc;
+        T.RP = P.RP;
+        T.r = P.rank;
+        T.Smax = P.Smax;
+        T.Cpad = P.Cpad;
+        T.FcT = ws + P.off_Fc;
+        T.Fi = S.Fi;
+        T.W = S.W;
+        T.part = S.part;
+        T.err = S.err;
+        grid = P.kind == ModeKind::Last ? dim3(P.G, P.n_cb, 1) : dim3(P.G, 1, 1);
+        smem = P.kind == ModeKind::Last ? tc_last_smem(P.RPH) : tc_rows_smem(P.RPH);
+        if (timer && timer->start) NTF_CUDA_TRY(record_timer_event(timer->start, st));
+        e = launch_stream_tc(kind, P.RPH, grid, smem, st, *map, T);
     } else {
-        grid = dim3(P.G, P.n_pb, 1);
-        smem = stream_rows_smem(v.es, P.RP);
+        if (P.kind == ModeKind::Last) {
+            grid = dim3(P.G, P.n_cb, P.n_pb);
+            smem = stream_last_smem(v.es, P.R);
+        } else {
+            grid = dim3(P.G, P.n_pb, 1);
+            smem = stream_rows_smem(v.es, P.RP);
+        }
+        if (timer && timer->start) NTF_CUDA_TRY(record_timer_event(timer->start, st));
+        e = v.dtype == NTF_F32 ? launch_stream_f32(kind, P.R, grid, smem, st, *map, S)
+                               : launch_stream_bf16(kind, P.R, grid, smem, st, *map, S);
     }
-    if (timer && timer->start) NTF_CUDA_TRY(cudaEventRecord(timer->start, st));
-    cudaError_t e = v.dtype == NTF_F32 ? launch_stream_f32(kind, P.R, grid, smem, st, *map, S)
-                                       : launch_stream_bf16(kind, P.R, grid, smem, st, *map, S);
     count_launch();
     if (e != cudaSuccess) return cuda_fail(e, "MTTKRP streaming kernel launch");
-    if (timer && timer->stop) NTF_CUDA_TRY(cudaEventRecord(timer->stop, st));
+    if (timer && timer->stop) NTF_CUDA_TRY(record_timer_event(timer->stop, st));
     return NTF_OK;
 }
 
@@ -342,11 +416,23 @@ ntf_status run_mttkrp(const TensorView& v, const MttkrpPlan& P, const float* con
 
     // 1. packed factors and weight table
     if (P.kind != ModeKind::Last) {
-        const int64_t rows_out = round_up(v.C, kStageCols);
-        k_pack<<<grid_for(rows_out * P.RP, 256), 256, 0, st>>>(factors[N - 1], v.C, r, P.RP, rows_out, Fc);
-        NTF_LAUNCH_CHECK("k_pack(A_last)");
+        if (P.tc) {
+            k_pack_fct<<<grid_for((int64_t)P.n_kc * 2 * P.RPH * 64, 256), 256, 0, st>>>(
+                factors[N - 1], v.C, r, P.RPH, P.n_kc, reinterpret_cast<__nv_bfloat16*>(Fc));
+            NTF_LAUNCH_CHECK("k_pack_fct");
+        } else {
+            const int64_t rows_out = round_up(v.C, kStageCols);
+            k_pack<<<grid_for(rows_out * P.RP, 256), 256, 0, st>>>(factors[N - 1], v.C, r, P.RP, rows_out, Fc);
+            NTF_LAUNCH_CHECK("k_pack(A_last)");
+        }
     }
-    if (P.kind != ModeKind::Inner) {
+    if (P.tc && P.kind == ModeKind::Last) {
+        // tensor-core operand of the last mode: A_{N-2} in 64-row chunks, two per 128-row block
+        const int chunks = (int)(2 * P.nb);
+        k_pack_fct<<<grid_for((int64_t)chunks * 2 * P.RPH * 64, 256), 256, 0, st>>>(
+            factors[N - 2], v.Ii, r, P.RPH, chunks, reinterpret_cast<__nv_bfloat16*>(Fc));
+        NTF_LAUNCH_CHECK("k_pack_fct(A_second_to_last)");
+    } else if (P.kind != ModeKind::Inner) {
         k_pack<<<grid_for(v.Ii * P.RP, 256), 256, 0, st>>>(factors[N - 2], v.Ii, r, P.RP, v.Ii, Fi);
         NTF_LAUNCH_CHECK("k_pack(A_second_to_last)");
     }
@@ -396,9 +482,16 @@ namespace ntf {
 // launching it (so that no attribute call happens inside a graph capture).
 ntf_status configure_mttkrp(const TensorView& v, const MttkrpPlan& P) {
     const int kind = P.kind == ModeKind::Inner ? 0 : P.kind == ModeKind::Outer ? 1 : 2;
-    const size_t smem = P.kind == ModeKind::Last ? stream_last_smem(v.es, P.R) : stream_rows_smem(v.es, P.RP);
     CUtensorMap dummy;
     std::memset(&dummy, 0, sizeof(dummy));
+    if (P.tc) {
+        TcParams T{};
+        const size_t smem = P.kind == ModeKind::Last ? tc_last_smem(P.RPH) : tc_rows_smem(P.RPH);
+        cudaError_t e = launch_stream_tc(kind, P.RPH, dim3(0, 1, 1), smem, nullptr, dummy, T);
+        if (e != cudaSuccess) return cuda_fail(e, "configure MTTKRP kernel");
+        return NTF_OK;
+    }
+    const size_t smem = P.kind == ModeKind::Last ? stream_last_smem(v.es, P.R) : stream_rows_smem(v.es, P.RP);
     StreamParams S{};
     cudaError_t e = v.dtype == NTF_F32 ? launch_stream_f32(kind, P.R, dim3(0, 1, 1), smem, nullptr, dummy, S)
                                        : launch_stream_bf16(kind, P.R, dim3(0, 1, 1), smem, nullptr, dummy, S);

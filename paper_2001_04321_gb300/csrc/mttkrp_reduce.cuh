@@ -7,12 +7,11 @@
 
 namespace ntf {
 
-constexpr int kPartWarps = 8;   // per-warp partial slots of the inner-mode stream
-
 struct ReduceParams {
     int kind;                     // 0 inner, 1 outer, 2 last
     int64_t n_tiles, n_ot, nb, Ii, n_o, C, Cpad;
     int G, Smax, I_T, RP, r;
+    int part_warps;               // inner mode: partial slots per CTA (8 per-warp, or 1)
     int64_t In, stride, hi_count;  // outer mode: o = (hi*In + j)*stride + lo
     const float* part;
     const float* W;
@@ -25,18 +24,20 @@ __device__ __forceinline__ float reduce_inner(const ReduceParams& P, int64_t j, 
     const int64_t ib = j / P.I_T;
     const int b = (int)(j % P.I_T);
     const int64_t t0 = ib * P.n_ot, t1 = t0 + P.n_ot;   // tiles of block ib
-    int g = (int)((t0 * P.G) / P.n_tiles);
-    while (g > 0 && (P.n_tiles * g) / P.G > t0) --g;
+    // CTA g owns tiles [floor(n_tiles g / G), floor(n_tiles (g+1) / G)); the CTA owning tile t is
+    // floor(((t + 1) G - 1) / n_tiles)
+    const int g0 = (int)(((t0 + 1) * P.G - 1) / P.n_tiles);
+    const int g1 = (int)((t1 * P.G - 1) / P.n_tiles);
+    // CTA g0 may have started in an earlier block (segment ib - its first block); every later
+    // CTA that meets block ib starts inside it (segment 0)
+    const int seg0 = (int)(ib - ((P.n_tiles * g0) / P.G) / P.n_ot);
+    const int64_t slot = (int64_t)P.part_warps * P.I_T * P.RP;          // one (CTA, segment) slot
+    const float* q = P.part + (int64_t)b * P.RP + p;
     float s = 0.f;
-    for (; g < P.G; ++g) {
-        const int64_t tb = (P.n_tiles * g) / P.G, te = (P.n_tiles * (g + 1)) / P.G;
-        if (tb >= t1) break;
-        if (te <= t0 || te <= tb) continue;
-        const int seg = (int)(ib - tb / P.n_ot);
-        const float* q = P.part + ((((int64_t)g * P.Smax + seg) * kPartWarps) * P.I_T + b) * P.RP + p;
-#pragma unroll
-        for (int w = 0; w < kPartWarps; ++w) s += q[(int64_t)w * P.I_T * P.RP];
-    }
+    for (int w = 0; w < P.part_warps; ++w) s += q[((int64_t)g0 * P.Smax + seg0) * slot + (int64_t)w * P.I_T * P.RP];
+#pragma unroll 8
+    for (int g = g0 + 1; g <= g1; ++g)
+        for (int w = 0; w < P.part_warps; ++w) s += q[((int64_t)g * P.Smax) * slot + (int64_t)w * P.I_T * P.RP];
     return s;
 }
 
@@ -48,6 +49,7 @@ __device__ __forceinline__ float reduce_outer(const ReduceParams& P, int64_t j, 
         for (int64_t lo = 0; lo < P.stride; ++lo) {
             const int64_t o = (hi * P.In + j) * P.stride + lo;
             float so = 0.f;
+#pragma unroll 4
             for (int64_t ib = 0; ib < P.nb; ++ib) so += P.part[(o * P.nb + ib) * P.RP + p];
             s = fmaf(P.W[o * P.RP + p], so, s);
         }
@@ -57,6 +59,7 @@ __device__ __forceinline__ float reduce_outer(const ReduceParams& P, int64_t j, 
 // Last mode: one partial per streaming CTA along the tile axis.
 __device__ __forceinline__ float reduce_last(const ReduceParams& P, int64_t c, int p) {
     float s = 0.f;
+#pragma unroll 8
     for (int g = 0; g < P.G; ++g) s += P.part[((int64_t)g * P.Cpad + c) * P.RP + p];
     return s;
 }

@@ -1,0 +1,542 @@
+// Tensor-core (tcgen05, kind::f16) MTTKRP streaming kernels for bfloat16
+// tensor storage (step a1; Sec. 2, def:B / def:grad: M_n = T_[n] B^n).
+//
+// The tensor tile is the A operand exactly as TMA lands it (128 rows x 64
+// bf16 columns, 128-byte swizzle).  The other operand carries a factor split
+// into bfloat16 high and low parts (x = hi + lo, |x - hi - lo| <= 2^-16 |x|),
+// side by side along N, so one MMA gives T*hi and T*lo in FP32 and their sum
+// is accurate to FP32 level while T itself is exact in bf16.
+//
+//   rows kernel (modes < N-1): D[row][p] = sum_k T[row][k] F[k][p], F = A_{N-1};
+//       A = T tile (K-major), B = F chunk stored [p][k] (K-major), one TMEM
+//       accumulator per 64-column chunk in a ring of four; 4 epilogue warps read
+//       one row per thread and apply the inner / outer weighting of the FFMA kernels.
+//   last kernel (mode N-1): per tile (one outer index o, 128 inner rows i)
+//       D[c][p] = sum_i T[(o,i)][c] A_{N-2}[i][p]; A = T tile (MN-major: its
+//       contiguous dimension is c), B = packed bf16 hi|lo rows of A_{N-2}
+//       (K-major); the epilogue folds W(o,p) D[c][p] into FP32 registers.
+//
+// The tensor cores' FP32 accumulation is not round-to-nearest (measured: a
+// consistent relative bias of about -8e-7 per accumulated MMA step), so no
+// TMEM accumulator takes more than 8 MMA steps: the rows kernel starts a fresh
+// accumulator for every 64-column chunk (4 steps), the last-mode kernel for
+// every tile (8 steps), and the epilogue sums them in registers with IEEE FP32.
+// The Khatri-Rao matrix is never formed: the last mode's weights W(o,:) enter
+// in the epilogue, per tile.
+//
+// Warps: 0-3 epilogue / Khatri-Rao builders (TMEM lanes 0-127), 4 TMA
+// producer, 5 MMA issuer (and TMEM owner).  Every wait is bounded.
+#include "mttkrp_kernels.cuh"
+#include "mttkrp_tc.cuh"
+
+namespace ntf {
+namespace {
+
+constexpr int kTcThreads = 192;
+constexpr int kTcStages = 4;
+constexpr int kDbuf = 4;             // rows kernel: TMEM accumulators in flight (64 columns each)
+constexpr int kBoxBytes = 16384;   // 128 rows x 64 bf16
+
+// ----------------------------------------------------------------------------
+// tcgen05 / descriptor helpers
+// ----------------------------------------------------------------------------
+// Shared-memory matrix descriptor (SM100 UMMA): start address, leading and
+// stride byte offsets (16-byte units), version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr, uint32_t lbo_bytes, uint32_t sbo_bytes) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, A and B bf16.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn_major, int b_mn_major) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) | ((uint32_t)b_mn_major << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 32 lanes x 32 bit, 16 consecutive columns per thread
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity) {
+    const bool mine = mbar_wait_bounded(bar, parity);
+    return __all_sync(0xffffffffu, mine) != 0;
+}
+
+// D columns [col0, col0 + 2*RPH) of this thread's TMEM lane -> y[p] = hi + lo
+template <int RPH>
+__device__ __forceinline__ void read_rows(uint32_t tmem_row, int col0, float (&y)[RPH]) {
+    float d[2 * RPH];
+#pragma unroll
+    for (int c = 0; c < 2 * RPH; c += 16) {
+        float v[16];
+        tmem_ld16(tmem_row + col0 + c, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) d[c + i] = v[i];
+    }
+    tmem_wait_ld();
+#pragma unroll
+    for (int p = 0; p < RPH; ++p) y[p] = d[p] + d[RPH + p];
+}
+
+// ----------------------------------------------------------------------------
+// rows kernel (inner / outer modes)
+// ----------------------------------------------------------------------------
+template <int RPH, bool INNER>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
+    constexpr int N = 2 * RPH;
+    constexpr int kB = N * 128;                 // factor chunk: N rows x 64 bf16 (swizzled)
+    constexpr int kStage = kBoxBytes + kB;      // multiple of 1024 (N multiple of 16)
+    constexpr uint32_t kIdesc = idesc_bf16(128, N, 0, 0);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* base_ptr = smem_raw + (base - raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base_ptr + kTcStages * kStage);
+    uint64_t* empty = full + kTcStages;
+    uint64_t* tfull = empty + kTcStages;        // [kDbuf]: accumulator of one 64-column chunk ready
+    uint64_t* tempty = tfull + kDbuf;           // [kDbuf]: accumulator read by the epilogue
+    uint64_t* drain = tempty + kDbuf;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    float* zsum = reinterpret_cast<float*>(base_ptr + kTcStages * kStage + 256);   // [2][4][32]
+    float* red = zsum + 2 * 4 * 32;                                                  // [128][RPH]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x, G = gridDim.x;
+    int64_t t_beg, t_end;
+    tile_range(P.n_tiles, g, G, t_beg, t_end);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < kDbuf; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(drain, 1);
+        fence_mbar_init();
+    }
+    if (warp == 5) tmem_alloc(tmem_slot, 64 * kDbuf);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 4) {
+        // ------------------------------ producer ------------------------------
+        if (lane == 0) {
+            prefetch_tensormap(&tmap);
+            int stage = 0;
+            uint32_t phase = 0;
+            int64_t issued = 0;
+            bool ok = true;
+            for (int64_t t = t_beg; t < t_end && ok; ++t) {
+                int64_t ib, ot;
+                if (INNER) { ib = t / P.n_ot; ot = t % P.n_ot; }
+                else { ot = t / P.nb; ib = t % P.nb; }
+                for (int kc = 0; kc < P.n_kc; ++kc) {
+                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
+                        record_device_error(P.err, kErrWaitEmpty);
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[stage], (uint32_t)kStage);
+                    unsigned char* st = base_ptr + stage * kStage;
+                    tma_load_3d(st, &tmap, &full[stage], kc * 64, (int)(ib * P.I_T), (int)(ot * P.O_T));
+                    bulk_load(st + kBoxBytes, P.FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
+                    ++issued;
+                    if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
+                }
+            }
+            drain_stages(full, stage, phase, issued, P.err);
+        }
+        return;
+    }
+
+    if (warp == 5) {
+        // ------------------------------ MMA issuer ------------------------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            int64_t gq = 0;   // accumulator (chunk) counter of this CTA
+            for (int64_t t = t_beg; t < t_end && ok; ++t) {
+                for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
+                    const int d = (int)(gq % kDbuf);
+                    if (!mbar_wait_bounded(&tempty[d], (uint32_t)((gq / kDbuf) & 1) ^ 1u) ||
+                        !mbar_wait_bounded(&full[stage], phase)) {
+                        record_device_error(P.err, kErrWaitFull);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = base + stage * kStage;
+                    const uint32_t b0 = a0 + kBoxBytes;
+                    const uint32_t dt = tmem + (uint32_t)(d * 64);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        tc_mma(dt, smem_desc_sw128(a0 + kk * 32, 16, 1024), smem_desc_sw128(b0 + kk * 32, 16, 1024),
+                               kIdesc, kk > 0 ? 1u : 0u);
+                    tc_commit(&empty[stage]);          // frees the stage once these MMAs have read it
+                    tc_commit(&tfull[d]);              // this chunk's accumulator is complete
+                    if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
+                }
+            }
+            // make sure nothing is still running on the tensor cores before TMEM is freed
+            tc_commit(drain);
+            if (!mbar_wait_bounded(drain, 0)) record_device_error(P.err, kErrWaitDrain);
+        }
+        __syncwarp();
+        named_bar_sync(2, 160);
+        tc_fence_after();
+        tmem_dealloc(tmem, 64 * kDbuf);
+        return;
+    }
+
+    // ------------------------------ epilogue (warps 0-3) ------------------------------
+    const int m = threadIdx.x;                       // tile row = TMEM lane
+    const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+    float macc[RPH];
+#pragma unroll
+    for (int p = 0; p < RPH; ++p) macc[p] = 0.f;
+    int64_t cur_ib = -1;
+    int seg = 0;
+    bool ok = true;
+    int64_t gq = 0;
+    int parity = 0;
+    auto flush_inner = [&](int s) {
+        // rows m, m + I_T, ... share inner row b = m % I_T of the block
+#pragma unroll
+        for (int p = 0; p < RPH; ++p) red[m * RPH + p] = macc[p];
+        named_bar_sync(1, 128);
+        if (m < P.I_T) {
+            for (int p = 0; p < P.r; ++p) {
+                float sacc = 0.f;
+                for (int a = 0; a < P.O_T; ++a) sacc += red[(a * P.I_T + m) * RPH + p];
+                P.part[(((int64_t)g * P.Smax + s) * P.I_T + m) * P.RP + p] = sacc;
+            }
+        }
+        named_bar_sync(1, 128);
+#pragma unroll
+        for (int p = 0; p < RPH; ++p) macc[p] = 0.f;
+    };
+    for (int64_t t = t_beg; t < t_end; ++t) {
+        int64_t ib, ot;
+        if (INNER) { ib = t / P.n_ot; ot = t % P.n_ot; }
+        else { ot = t / P.nb; ib = t % P.nb; }
+        if (INNER && ib != cur_ib) {
+            if (cur_ib >= 0) flush_inner(seg++);
+            cur_ib = ib;
+        }
+        // weights of this row, fetched while the tile is being contracted
+        float w[RPH];
+        bool row_live;
+        if (INNER) {
+            const int64_t o = ot * P.O_T + m / P.I_T;
+            row_live = o < P.n_o && ib * P.I_T + m % P.I_T < P.Ii;
+            const float* src = P.W + (row_live ? o : 0) * P.RP;
+#pragma unroll
+            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.RP) ? __ldg(src + p) : 0.f;
+        } else {
+            const int64_t i = ib * 128 + m;
+            row_live = i < P.Ii;
+            const float* src = P.Fi + (row_live ? i : 0) * P.RP;
+#pragma unroll
+            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.RP) ? __ldg(src + p) : 0.f;
+        }
+        // Y(row) = sum over the tile's 64-column chunks of the chunk accumulators (IEEE FP32 adds)
+        float y[RPH];
+#pragma unroll
+        for (int p = 0; p < RPH; ++p) y[p] = 0.f;
+        for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
+            const int d = (int)(gq % kDbuf);
+            if (ok && !warp_wait(&tfull[d], (uint32_t)((gq / kDbuf) & 1))) {
+                if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                ok = false;
+            }
+            if (ok) {
+                tc_fence_after();
+                float yc[RPH];
+                read_rows<RPH>(tmem_row, d * 64, yc);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[d]);
+#pragma unroll
+                for (int p = 0; p < RPH; ++p) y[p] += yc[p];
+            }
+        }
+        if (INNER) {
+#pragma unroll
+            for (int p = 0; p < RPH; ++p) macc[p] = fmaf(w[p], y[p], macc[p]);
+        } else {
+            float z[RPH];
+#pragma unroll
+            for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
+            float mine = 0.f;
+#pragma unroll
+            for (int p = 0; p < RPH; ++p)
+                if (p == lane) mine = z[p];
+            float* zs = zsum + parity * 128;
+            zs[warp * 32 + lane] = mine;
+            named_bar_sync(1, 128);
+            if (warp == 0 && lane < P.r && ok) {
+                const float s4 = (zs[lane] + zs[32 + lane]) + (zs[64 + lane] + zs[96 + lane]);
+                P.part[((ot * P.nb) + ib) * P.RP + lane] = s4;
+            }
+            parity ^= 1;
+        }
+    }
+    if (INNER && cur_ib >= 0) flush_inner(seg);
+    tc_fence_before();
+    named_bar_sync(2, 160);
+}
+
+// ----------------------------------------------------------------------------
+// last-mode kernel
+//   M(c,p) = sum_o W(o,p) * sum_i T((o,i),c) A_{N-2}(i,p)
+// A tile is one outer index o and 128 inner rows i of one 128-column block;
+// the inner sum is one MMA chain (A = T tile, MN-major; B = the packed bf16
+// hi|lo block of A_{N-2} for those rows, K-major), and the epilogue folds
+// W(o,:) times each tile's accumulator into FP32 registers.
+// ----------------------------------------------------------------------------
+template <int RPH>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
+    constexpr int N = 2 * RPH;
+    constexpr int kT = 2 * kBoxBytes;          // 128 rows x 128 columns (two 64-column boxes)
+    constexpr int kB = 2 * N * 128;            // A_{N-2} block: 2 K-atoms x N rows x 128 B
+    constexpr int kStage = kT + kB;
+    constexpr int kLastDbuf = 4;
+    constexpr uint32_t kIdesc = idesc_bf16(128, N, 1, 0);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* base_ptr = smem_raw + (base - raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base_ptr + kTcStages * kStage);
+    uint64_t* empty = full + kTcStages;
+    uint64_t* tfull = empty + kTcStages;        // [kLastDbuf]
+    uint64_t* tempty = tfull + kLastDbuf;       // [kLastDbuf]
+    uint64_t* drain = tempty + kLastDbuf;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x, G = gridDim.x;
+    const int cb = blockIdx.y;
+    int64_t t_beg, t_end;
+    tile_range(P.n_tiles, g, G, t_beg, t_end);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < kLastDbuf; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(drain, 1);
+        fence_mbar_init();
+    }
+    if (warp == 5) tmem_alloc(tmem_slot, 64 * kLastDbuf);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            prefetch_tensormap(&tmap);
+            int stage = 0;
+            uint32_t phase = 0;
+            int64_t issued = 0;
+            const int64_t left = P.C - (int64_t)cb * 128;
+            const int nbox = left > 64 ? 2 : 1;
+            for (int64_t t = t_beg; t < t_end; ++t) {
+                const int64_t ib = t / P.n_ot, o = t % P.n_ot;   // I_T = 128, O_T = 1
+                if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
+                    record_device_error(P.err, kErrWaitEmpty);
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[stage], (uint32_t)(nbox * kBoxBytes + kB));
+                unsigned char* st = base_ptr + stage * kStage;
+                for (int b = 0; b < nbox; ++b)
+                    tma_load_3d(st + b * kBoxBytes, &tmap, &full[stage], cb * 128 + b * 64, (int)(ib * 128), (int)o);
+                bulk_load(st + kT, P.FcT + ib * kB, (uint32_t)kB, &full[stage]);
+                ++issued;
+                if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
+            }
+            drain_stages(full, stage, phase, issued, P.err);
+        }
+        return;
+    }
+
+    if (warp == 5) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int64_t tl = 0;
+            for (int64_t t = t_beg; t < t_end; ++t, ++tl) {
+                const int d = (int)(tl % kLastDbuf);
+                if (!mbar_wait_bounded(&tempty[d], (uint32_t)((tl / kLastDbuf) & 1) ^ 1u) ||
+                    !mbar_wait_bounded(&full[stage], phase)) {
+                    record_device_error(P.err, kErrWaitFull);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = base + stage * kStage;
+                const uint32_t b0 = a0 + kT;
+                const uint32_t dt = tmem + (uint32_t)(d * 64);
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    // A: 16 tile rows (two 8-row groups 1024 B apart), 128 columns in two
+                    // 64-column blocks 16 KB apart; B: K-atom kk/4, 32-byte step kk%4
+                    const uint64_t ad = smem_desc_sw128(a0 + kk * 2048, kBoxBytes, 1024);
+                    const uint64_t bd = smem_desc_sw128(b0 + (kk >> 2) * (N * 128) + (kk & 3) * 32, 16, 1024);
+                    tc_mma(dt, ad, bd, kIdesc, kk > 0 ? 1u : 0u);
+                }
+                tc_commit(&empty[stage]);
+                tc_commit(&tfull[d]);
+                if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
+            }
+            tc_commit(drain);
+            if (!mbar_wait_bounded(drain, 0)) record_device_error(P.err, kErrWaitDrain);
+        }
+        __syncwarp();
+        named_bar_sync(2, 160);
+        tc_fence_after();
+        tmem_dealloc(tmem, 64 * kLastDbuf);
+        return;
+    }
+
+    // ---------------- warps 0-3: fold W(o,:) x tile accumulator into registers ----------------
+    const int m = threadIdx.x;
+    const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+    bool ok = true;
+    float acc[RPH];
+#pragma unroll
+    for (int p = 0; p < RPH; ++p) acc[p] = 0.f;
+    int64_t tl = 0;
+    for (int64_t t = t_beg; t < t_end; ++t, ++tl) {
+        const int64_t o = t % P.n_ot;
+        float w[RPH];
+        const float* wr = P.W + o * P.RP;
+#pragma unroll
+        for (int p = 0; p < RPH; ++p) w[p] = p < P.RP ? __ldg(wr + p) : 0.f;
+        const int d = (int)(tl % kLastDbuf);
+        if (ok && !warp_wait(&tfull[d], (uint32_t)((tl / kLastDbuf) & 1))) {
+            if (lane == 0) record_device_error(P.err, kErrWaitFull);
+            ok = false;
+        }
+        if (ok) {
+            tc_fence_after();
+            float y[RPH];
+            read_rows<RPH>(tmem_row, d * 64, y);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[d]);
+#pragma unroll
+            for (int p = 0; p < RPH; ++p) acc[p] = fmaf(w[p], y[p], acc[p]);
+        }
+    }
+    // row m of the result = column cb*128 + m of M_{N-1}
+    const int64_t c = (int64_t)cb * 128 + m;
+    if (ok && c < P.C) {
+        float* dst = P.part + ((int64_t)g * P.Cpad + c) * P.RP;
+#pragma unroll
+        for (int p = 0; p < RPH; ++p)
+            if (p < P.r) dst[p] = acc[p];
+    }
+    tc_fence_before();
+    named_bar_sync(2, 160);
+}
+
+template <int RPH>
+cudaError_t launch_tc_impl(int kind, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
+                           const TcParams& P) {
+    typedef void (*Kern)(const CUtensorMap, const TcParams);
+    Kern k = kind == 0 ? (Kern)k_tc_rows<RPH, true> : kind == 1 ? (Kern)k_tc_rows<RPH, false> : (Kern)k_tc_last<RPH>;
+    static size_t set_bytes[3] = {0, 0, 0};
+    if (set_bytes[kind] < smem) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_bytes[kind] = smem;
+    }
+    if (grid.x == 0) return cudaSuccess;
+    k<<<grid, kTcThreads, smem, st>>>(map, P);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc_rows_smem(int rph) {
+    const int N = 2 * rph;
+    return (size_t)kTcStages * (kBoxBytes + N * 128) + 1024 + 256 + 2 * 4 * 32 * 4 + 128 * rph * 4;
+}
+// (barrier block: 4 full + 4 empty + kDbuf tfull + kDbuf tempty + drain + TMEM slot < 256 bytes)
+size_t tc_last_smem(int rph) {
+    const int N = 2 * rph;
+    return (size_t)kTcStages * (2 * kBoxBytes + 2 * N * 128) + 1024 + 256;
+}
+// bytes of the packed A_{N-2} operand of the last-mode kernel per 128-row block
+size_t tc_last_b_bytes(int rph) { return (size_t)2 * (2 * rph) * 128; }
+
+cudaError_t launch_stream_tc(int kind, int rph, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
+                             const TcParams& P) {
+    switch (rph) {
+        case 8: return launch_tc_impl<8>(kind, grid, smem, st, map, P);
+        case 16: return launch_tc_impl<16>(kind, grid, smem, st, map, P);
+        case 24: return launch_tc_impl<24>(kind, grid, smem, st, map, P);
+        case 32: return launch_tc_impl<32>(kind, grid, smem, st, map, P);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace ntf

@@ -1,0 +1,30 @@
+// tcgen05 MTTKRP kernels for bf16 tensor storage (see mttkrp_tc.cu).
+#pragma once
+
+#include "ntf_common.cuh"
+
+namespace ntf {
+
+struct TcParams {
+    int64_t C, Ii, n_o;
+    int I_T, O_T;
+    int64_t nb, n_ot, n_tiles;
+    int n_kc;
+    int RP, r;
+    int Smax;
+    int64_t Cpad;
+    const unsigned char* FcT;   // rows kernel: A_{N-1} per 64-row chunk; last kernel: A_{N-2} per 128-row
+                                // block; N rows x 128 B per 64 rows, swizzled bf16 hi|lo
+    const float* Fi;            // packed A_{N-2}: Ii x RP (fp32)
+    const float* W;             // n_o x RP (fp32)
+    float* part;
+    int* err;
+};
+
+size_t tc_rows_smem(int rph);
+size_t tc_last_smem(int rph);
+size_t tc_last_b_bytes(int rph);
+cudaError_t launch_stream_tc(int kind, int rph, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
+                             const TcParams& P);
+
+}  // namespace ntf

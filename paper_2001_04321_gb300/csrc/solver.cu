@@ -19,6 +19,12 @@ struct Solver {
     void* owned_T = nullptr; // device copy made by ntf_solve_host
     int N = 0, r = 0;
     ntf_opts o;
+    // two buffers per mode (factor and Gram); the fused path flips cur[] on an
+    // accepted extrapolation, the general path keeps A in buffer 0 and copies
+    float* X[NTF_MAX_ORDER][2] = {{nullptr}};
+    double* GB[NTF_MAX_ORDER][2] = {{nullptr}};
+    int* cur = nullptr;         // device [NTF_MAX_ORDER]
+    int* iters_dev = nullptr;   // device: completed outer iterations
     float* A[NTF_MAX_ORDER] = {nullptr};
     float* Ah[NTF_MAX_ORDER] = {nullptr};
     double* G[NTF_MAX_ORDER] = {nullptr};   // Grams of A
@@ -45,10 +51,14 @@ struct Solver {
     bool fused = false;
     float* gpart = nullptr;
     double* ipart = nullptr;
-    unsigned* ticket = nullptr;
-    // graph replay
+    double* qpart = nullptr;
+    // graph replay: one graph holds g_iters outer iterations (and, when timing is
+    // on, the event records around each MTTKRP stream, read after the replay)
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
+    int g_iters = 0;
+    bool g_timing = false;
+    int64_t g_kernels = 0;   // kernel nodes in the graph
 
     ~Solver() {
         if (gexec) cudaGraphExecDestroy(gexec);
@@ -99,14 +109,29 @@ struct Solver {
         return P;
     }
 
+    FusedBufs fused_bufs() const {
+        FusedBufs B{};
+        for (int l = 0; l < N; ++l)
+            for (int k = 0; k < 2; ++k) {
+                B.X[l][k] = X[l][k];
+                B.GB[l][k] = GB[l][k];
+            }
+        B.cur = cur;
+        B.iters = iters_dev;
+        B.her = o.her;
+        return B;
+    }
+
     // one outer iteration on the fused path: per mode prep -> stream -> epilogue,
-    // then (HER) the accept/restart copies decided by the last epilogue
+    // then one small kernel for F_hat, the decision and the buffer flip
     ntf_status iterate_fused(cudaStream_t st) {
         const bool use_her = o.her != 0;
         unsigned char* ws = static_cast<unsigned char*>(ws_mt);
+        const FusedBufs fb = fused_bufs();
         for (int n = 0; n < N; ++n) {
             const MttkrpPlan& P = plan[n];
             PrepParams pp{};
+            pp.B = fb;
             pp.order = N;
             pp.mode = n;
             pp.skip = P.kind == ModeKind::Outer ? n : -1;
@@ -116,44 +141,69 @@ struct Solver {
             pp.Ii = vs.Ii;
             pp.n_o = vs.n_o;
             pp.Fc_rows_out = round_up(vs.C, 64);
-            for (int l = 0; l < N; ++l) {
-                pp.dims[l] = vs.dims[l];
-                pp.A[l] = Ah[l];
-                pp.Gh[l] = Gh[l];
-            }
+            for (int l = 0; l < N; ++l) pp.dims[l] = vs.dims[l];
             pp.V = V;
-            pp.Fc = P.kind != ModeKind::Last ? reinterpret_cast<float*>(ws + P.off_Fc) : nullptr;
-            pp.Fi = P.kind != ModeKind::Inner ? reinterpret_cast<float*>(ws + P.off_Fi) : nullptr;
+            pp.Fc = (P.kind != ModeKind::Last && !P.tc) ? reinterpret_cast<float*>(ws + P.off_Fc) : nullptr;
+            pp.FcT = P.tc ? reinterpret_cast<__nv_bfloat16*>(ws + P.off_Fc) : nullptr;
+            pp.RPH = P.RPH;
+            if (P.kind == ModeKind::Last) {      // tensor-core last mode: A_{N-2}, two chunks per 128-row block
+                pp.fct_mode = N - 2;
+                pp.fct_rows = vs.Ii;
+                pp.n_kc = (int)(2 * P.nb);
+            } else {
+                pp.fct_mode = N - 1;
+                pp.fct_rows = vs.C;
+                pp.n_kc = P.n_kc;
+            }
+            pp.Fi = (P.kind != ModeKind::Inner && !(P.tc && P.kind == ModeKind::Last))
+                        ? reinterpret_cast<float*>(ws + P.off_Fi)
+                        : nullptr;
             pp.W = reinterpret_cast<float*>(ws + P.off_W);
+            pp.fin_mode = n > 0 ? n - 1 : N - 1;
+            pp.fin_blocks = epilogue_blocks(vs.dims[pp.fin_mode]);
+            pp.gpart = gpart;
+            pp.her = use_her ? her : nullptr;
             cudaError_t e = launch_prep(pp, st);
             if (e != cudaSuccess) return cuda_fail(e, "prep");
             ntf_status s = run_mttkrp_stream(vs, P, ws_mt, st, &tm[n], next_timer());
             if (s != NTF_OK) return s;
             EpiParams ep{};
+            ep.B = fb;
             ep.red = make_reduce_params(vs, P, reinterpret_cast<const float*>(ws + P.off_part),
                                         reinterpret_cast<const float*>(ws + P.off_W));
+            ep.mode = n;
             ep.rows = vs.dims[n];
             ep.r = r;
-            ep.A = A[n];
-            ep.Ah = use_her ? Ah[n] : nullptr;
+            ep.last = n == N - 1 ? 1 : 0;
             ep.beta = &her->beta;
             ep.V = V;
             ep.gpart = gpart;
             ep.ipart = ipart;
-            ep.ticket = ticket;
-            ep.G_out = use_her ? G[n] : Gh[n];
-            ep.Gh_out = use_her ? Gh[n] : nullptr;
-            ep.last = n == N - 1 ? 1 : 0;
-            ep.tnorm = &scal[0];
-            ep.fhat_out = &scal[1];
-            ep.her = use_her ? her : nullptr;
+            ep.qpart = qpart;
             e = launch_epilogue(ep, st);
             if (e != cudaSuccess) return cuda_fail(e, "epilogue");
         }
-        if (use_her) {
-            cudaError_t e = launch_her_copy(her, her_pairs(), st);
-            if (e != cudaSuccess) return cuda_fail(e, "her copy");
-        }
+        FinishParams fp{};
+        fp.B = fb;
+        fp.order = N;
+        fp.blocks = epilogue_blocks(vs.dims[N - 1]);
+        fp.ipart = ipart;
+        fp.qpart = qpart;
+        fp.tnorm = &scal[0];
+        fp.fhat_out = &scal[1];
+        fp.iters_out = iters_dev;
+        fp.her = use_her ? her : nullptr;
+        cudaError_t e = launch_finish(fp, st);
+        if (e != cudaSuccess) return cuda_fail(e, "finish");
+        return NTF_OK;
+    }
+
+    // device pointers of the current factors A_k (synchronises `st`)
+    ntf_status current_factors(cudaStream_t st, float** out) {
+        int h[NTF_MAX_ORDER] = {0};
+        NTF_CUDA_TRY(cudaMemcpyAsync(h, cur, sizeof(int) * NTF_MAX_ORDER, cudaMemcpyDeviceToHost, st));
+        NTF_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int l = 0; l < N; ++l) out[l] = X[l][h[l] & 1];
         return NTF_OK;
     }
 
@@ -210,11 +260,14 @@ struct Solver {
         float* W = static_cast<float*>(ws_res);
         const size_t woff = ((sizeof(float) * (size_t)v.n_o * RP) + 255) & ~size_t(255);
         double* parts = reinterpret_cast<double*>(static_cast<unsigned char*>(ws_res) + woff);
+        float* facs[NTF_MAX_ORDER];
+        ntf_status s = current_factors(st, facs);
+        if (s != NTF_OK) return s;
         const float* fac[NTF_MAX_ORDER];
-        for (int l = 0; l < N; ++l) fac[l] = A[l];
+        for (int l = 0; l < N; ++l) fac[l] = facs[l];
         cudaError_t e = launch_weights_all(v, fac, r, RP, W, st);
         if (e != cudaSuccess) return cuda_fail(e, "residual weights");
-        e = launch_residual_sq(v, r, W, RP, A[N - 2], A[N - 1], parts, out, st);
+        e = launch_residual_sq(v, r, W, RP, fac[N - 2], fac[N - 1], parts, out, st);
         if (e != cudaSuccess) return cuda_fail(e, "residual");
         return NTF_OK;
     }
@@ -289,18 +342,20 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     for (int l = 0; l < N; ++l) maxrows = std::max(maxrows, S->vu.dims[l]);
     for (int l = 0; l < N; ++l) {
         const size_t fb = sizeof(float) * (size_t)S->vu.dims[l] * r;
-        if ((s = S->alloc((void**)&S->A[l], fb)) != NTF_OK) return bail(s);
-        NTF_CUDA_TRY(cudaMemcpyAsync(S->A[l], factors[l], fb, cudaMemcpyDeviceToDevice, st));
-        if ((s = S->alloc((void**)&S->G[l], sizeof(double) * r * r)) != NTF_OK) return bail(s);
-        if (S->o.her) {
-            if ((s = S->alloc((void**)&S->Ah[l], fb)) != NTF_OK) return bail(s);
-            NTF_CUDA_TRY(cudaMemcpyAsync(S->Ah[l], factors[l], fb, cudaMemcpyDeviceToDevice, st));  // A_hat_0 = A_0
-            if ((s = S->alloc((void**)&S->Gh[l], sizeof(double) * r * r)) != NTF_OK) return bail(s);
-        } else {
-            S->Ah[l] = S->A[l];
-            S->Gh[l] = S->G[l];
+        for (int k = 0; k < 2; ++k) {
+            if ((s = S->alloc((void**)&S->X[l][k], fb)) != NTF_OK) return bail(s);
+            NTF_CUDA_TRY(cudaMemcpyAsync(S->X[l][k], factors[l], fb, cudaMemcpyDeviceToDevice, st));  // A_hat_0 = A_0
+            if ((s = S->alloc((void**)&S->GB[l][k], sizeof(double) * r * r)) != NTF_OK) return bail(s);
         }
+        S->A[l] = S->X[l][0];
+        S->G[l] = S->GB[l][0];
+        S->Ah[l] = S->o.her ? S->X[l][1] : S->X[l][0];
+        S->Gh[l] = S->o.her ? S->GB[l][1] : S->GB[l][0];
     }
+    if ((s = S->alloc((void**)&S->cur, sizeof(int) * NTF_MAX_ORDER)) != NTF_OK) return bail(s);
+    if ((s = S->alloc((void**)&S->iters_dev, 256)) != NTF_OK) return bail(s);
+    NTF_CUDA_TRY(cudaMemsetAsync(S->cur, 0, sizeof(int) * NTF_MAX_ORDER, st));
+    NTF_CUDA_TRY(cudaMemsetAsync(S->iters_dev, 0, 256, st));
     if ((s = S->alloc((void**)&S->Aprev, sizeof(float) * maxrows * r)) != NTF_OK) return bail(s);
     if ((s = S->alloc((void**)&S->M, sizeof(float) * maxrows * r)) != NTF_OK) return bail(s);
     if ((s = S->alloc((void**)&S->V, sizeof(double) * r * r)) != NTF_OK) return bail(s);
@@ -319,8 +374,7 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
         const int64_t blocks = epilogue_blocks(maxrows);
         if ((s = S->alloc((void**)&S->gpart, sizeof(float) * (size_t)blocks * 2 * r * r)) != NTF_OK) return bail(s);
         if ((s = S->alloc((void**)&S->ipart, sizeof(double) * (size_t)blocks)) != NTF_OK) return bail(s);
-        if ((s = S->alloc((void**)&S->ticket, 256)) != NTF_OK) return bail(s);
-        NTF_CUDA_TRY(cudaMemsetAsync(S->ticket, 0, 256, st));
+        if ((s = S->alloc((void**)&S->qpart, sizeof(double) * (size_t)blocks)) != NTF_OK) return bail(s);
     }
     S->ws_res_bytes = (((sizeof(float) * (size_t)S->vu.n_o * round_up(r, 4)) + 255) & ~size_t(255)) +
                       sizeof(double) * (size_t)std::max(stream_red_blocks(), 1);
@@ -341,9 +395,9 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     if (e != cudaSuccess) return bail(cuda_fail(e, "norm"));
     // Grams of A_0 (= A_hat_0)
     for (int l = 0; l < N; ++l) {
-        e = launch_gram(S->A[l], S->vu.dims[l], r, S->G[l], st);
+        e = launch_gram(S->X[l][0], S->vu.dims[l], r, S->GB[l][0], st);
         if (e != cudaSuccess) return bail(cuda_fail(e, "gram"));
-        if (S->o.her) NTF_CUDA_TRY(cudaMemcpyAsync(S->Gh[l], S->G[l], sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+        NTF_CUDA_TRY(cudaMemcpyAsync(S->GB[l][1], S->GB[l][0], sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
     }
     // F-hat_0 = ||T - [[A_0]]||^2 explicitly (on the streamed tensor)
     if ((s = S->residual(S->vs, &S->scal[3], st)) != NTF_OK) return bail(s);
@@ -354,33 +408,59 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     return NTF_OK;
 }
 
+constexpr int kMaxGraphIters = 1024;
+
+// Capture `iters` outer iterations into one executable graph.
+static ntf_status capture_graph(Solver* S, int iters, cudaStream_t st) {
+    if (S->gexec) {
+        cudaGraphExecDestroy(S->gexec);
+        S->gexec = nullptr;
+    }
+    S->ev_used = 0;   // the graph's event records use the first timers of the pool
+    cudaGraph_t g;
+    const int64_t before = ntf_launch_count();
+    NTF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    ntf_status s = NTF_OK;
+    for (int k = 0; k < iters && s == NTF_OK; ++k) s = S->iterate(st);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    // capturing launches nothing: the kernels are counted when the graph is replayed
+    S->g_kernels = ntf_launch_count() - before;
+    count_launch(-(int)S->g_kernels);
+    if (s != NTF_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&S->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    S->gstream = st;
+    S->g_iters = iters;
+    S->g_timing = S->timing;
+    return NTF_OK;
+}
+
 static ntf_status run_solver(Solver* S, int iters, cudaStream_t st) {
     if (iters < 0) return fail(NTF_EINVAL, "iters must be >= 0");
-    const bool graph = S->o.use_graph && st != nullptr && !S->timing;
-    for (int k = 0; k < iters; ++k) {
-        if (graph) {
-            if (!S->gexec || S->gstream != st) {
-                if (S->gexec) {
-                    cudaGraphExecDestroy(S->gexec);
-                    S->gexec = nullptr;
-                }
-                cudaGraph_t g;
-                NTF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-                ntf_status s = S->iterate(st);
-                cudaError_t e = cudaStreamEndCapture(st, &g);
-                if (s != NTF_OK) return s;
-                if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-                e = cudaGraphInstantiate(&S->gexec, g, 0);
-                cudaGraphDestroy(g);
-                if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-                S->gstream = st;
-            }
-            NTF_CUDA_TRY(cudaGraphLaunch(S->gexec, st));
-        } else {
+    const bool graph = S->o.use_graph && st != nullptr;
+    if (!graph) {
+        for (int k = 0; k < iters; ++k) {
             ntf_status s = S->iterate(st);
             if (s != NTF_OK) return s;
+            ++S->iters_done;
         }
-        ++S->iters_done;
+        return NTF_OK;
+    }
+    if (S->timing && iters > kMaxGraphIters)
+        return fail(NTF_EINVAL, "timed graph runs are limited to 1024 iterations per call");
+    int left = iters;
+    while (left > 0) {
+        const int chunk = left < kMaxGraphIters ? left : kMaxGraphIters;
+        if (!S->gexec || S->gstream != st || S->g_iters != chunk || S->g_timing != S->timing) {
+            ntf_status s = capture_graph(S, chunk, st);
+            if (s != NTF_OK) return s;
+        }
+        NTF_CUDA_TRY(cudaGraphLaunch(S->gexec, st));
+        count_launch((int)S->g_kernels);
+        left -= chunk;
+        S->iters_done += chunk;
     }
     return NTF_OK;
 }
@@ -439,9 +519,12 @@ ntf_status ntf_solver_get_factors(ntf_solver* h, float* const* factors, void* st
     if (!h || !h->s) return fail(NTF_EINVAL, "solver is NULL");
     if (!factors) return fail(NTF_EINVAL, "factors is NULL");
     Solver* S = h->s;
+    float* src[NTF_MAX_ORDER];
+    ntf_status s = S->current_factors(static_cast<cudaStream_t>(stream), src);
+    if (s != NTF_OK) return s;
     for (int l = 0; l < S->N; ++l) {
         if (!factors[l]) return fail(NTF_EINVAL, "factor pointer is NULL");
-        NTF_CUDA_TRY(cudaMemcpyAsync(factors[l], S->A[l], sizeof(float) * S->vu.dims[l] * S->r,
+        NTF_CUDA_TRY(cudaMemcpyAsync(factors[l], src[l], sizeof(float) * S->vu.dims[l] * S->r,
                                      cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
     }
     return NTF_OK;
@@ -452,10 +535,18 @@ ntf_status ntf_solver_report(ntf_solver* h, ntf_report* report, void* stream) {
     return solver_report(h->s, report, static_cast<cudaStream_t>(stream));
 }
 
+ntf_status ntf_solver_prepare_graph(ntf_solver* h, int iters, void* stream) {
+    if (!h || !h->s) return fail(NTF_EINVAL, "solver is NULL");
+    if (iters < 1 || iters > kMaxGraphIters) return fail(NTF_EINVAL, "iters must be in [1, 1024]");
+    if (!stream) return fail(NTF_EINVAL, "graph capture needs a non-default stream");
+    if (!h->s->o.use_graph) return fail(NTF_EINVAL, "the solver was created without opts.use_graph");
+    return capture_graph(h->s, iters, static_cast<cudaStream_t>(stream));
+}
+
 ntf_status ntf_solver_set_timing(ntf_solver* h, int on) {
     if (!h || !h->s) return fail(NTF_EINVAL, "solver is NULL");
     h->s->timing = on != 0;
-    h->s->ev_used = 0;
+    if (!h->s->gexec) h->s->ev_used = 0;
     return NTF_OK;
 }
 
@@ -473,7 +564,7 @@ ntf_status ntf_solver_mttkrp_time(ntf_solver* h, double* total_ms, int64_t* laun
     if (total_ms) *total_ms = tot;
     if (launches) *launches = (int64_t)S->ev_used;
     if (bytes_per_launch) *bytes_per_launch = (double)S->vs.numel() * S->vs.es;
-    S->ev_used = 0;
+    if (!S->gexec) S->ev_used = 0;   // eager timers are reused; a graph keeps its own
     return NTF_OK;
 }
 
@@ -497,9 +588,11 @@ ntf_status ntf_solve(const ntf_tensor* T, float* const* factors, int rank, const
         if (e != cudaSuccess) s = cuda_fail(e, "solve");
     }
     S->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    float* src[NTF_MAX_ORDER];
+    if (s == NTF_OK) s = S->current_factors(st, src);
     if (s == NTF_OK) {
         for (int l = 0; l < S->N && s == NTF_OK; ++l) {
-            cudaError_t e = cudaMemcpyAsync(factors[l], S->A[l], sizeof(float) * S->vu.dims[l] * rank,
+            cudaError_t e = cudaMemcpyAsync(factors[l], src[l], sizeof(float) * S->vu.dims[l] * rank,
                                             cudaMemcpyDeviceToDevice, st);
             if (e != cudaSuccess) s = cuda_fail(e, "copy factors");
         }
@@ -566,9 +659,11 @@ ntf_status ntf_solve_host(const ntf_tensor* T_host, float* const* factors_host, 
     }
     auto t0 = std::chrono::steady_clock::now();
     s = run_solver(S, S->o.max_iters, st);
+    float* src[NTF_MAX_ORDER];
+    if (s == NTF_OK) s = S->current_factors(st, src);
     if (s == NTF_OK) {
         for (int l = 0; l < S->N; ++l)
-            cudaMemcpyAsync(factors_host[l], S->A[l], sizeof(float) * S->vu.dims[l] * rank, cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(factors_host[l], src[l], sizeof(float) * S->vu.dims[l] * rank, cudaMemcpyDeviceToHost, st);
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) s = cuda_fail(e, "solve");
     }

@@ -147,3 +147,32 @@ def test_graph_replay_matches_eager():
         r2 = ntf.solve(buf, F2, ntf.Opts(max_iters=12, use_graph=True), dims=d, ld=ld)
     assert r1.f_true_last == r2.f_true_last
     assert all(torch.equal(a, b) for a, b in zip(F1, F2))
+
+
+def test_prepared_graph_with_timing_matches_eager():
+    import torch
+    import paper_2001_04321_gb300 as ntf
+    dims, r = (40, 30, 20), 5
+    T, init, buf, d, ld, Fd = _setup(dims, r, 1e-2, 14)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(st):
+        F1 = [A.clone() for A in Fd]
+        s1 = ntf.Solver(buf, F1, ntf.Opts(), dims=d, ld=ld)
+        s1.run(8)
+        s1.get_factors(F1)
+        F2 = [A.clone() for A in Fd]
+        s2 = ntf.Solver(buf, F2, ntf.Opts(use_graph=True), dims=d, ld=ld)
+        s2.run(3)
+        s2.set_timing(True)
+        s2.prepare_graph(5)
+        before = ntf.launch_count()
+        s2.run(5)
+        ms, n, nbytes = s2.mttkrp_time()
+        assert ntf.launch_count() - before >= 5 * 3 * 3
+        s2.get_factors(F2)
+        st.synchronize()
+    assert n == 15 and ms > 0 and nbytes == T.size * 4
+    assert all(torch.equal(a, b) for a, b in zip(F1, F2))
+    s1.close()
+    s2.close()
