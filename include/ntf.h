@@ -233,6 +233,18 @@ NTF_API ntf_status ntf_bcd_update(ntf_method method, float* A, int64_t rows, int
                           int inner_max, double inner_tol, void* workspace, size_t ws_bytes, void* stream);
 
 /* ----------------------------------------------------------------------- */
+/* Step a9 helper: block gradient of the CP loss                             */
+/* ----------------------------------------------------------------------- */
+
+/* out (rows x rank, float32) <- s (A V - M), the gradient of (1/2)||T - X||^2
+ * with respect to the factor A (Sec. 2, eq. def:grad: (A B^T - T_[n]) B with
+ * B^T B = V, the Hadamard product of the other Grams (Appendix A), and
+ * T_[n] B = M, the MTTKRP).  s = scale * (*scale_dev) if scale_dev is not
+ * NULL (device float64, e.g. an autograd upstream gradient), else scale. */
+NTF_API ntf_status ntf_block_gradient(const float* A, int64_t rows, int rank, const float* M, const double* V,
+                                      const double* scale_dev, double scale, float* out, void* stream);
+
+/* ----------------------------------------------------------------------- */
 /* Step a4: HER extrapolation (Alg. 2, eq. extproj_her)                       */
 /* ----------------------------------------------------------------------- */
 

@@ -49,6 +49,7 @@ def _load():
             lib = C.CDLL(_LIB)
             lib.oracle_mttkrp.argtypes = [C.c_int, _I64, _D, C.POINTER(_D), C.c_int, C.c_int, _D]
             lib.oracle_mttkrp_kr.argtypes = lib.oracle_mttkrp.argtypes
+            lib.oracle_cp_gradient.argtypes = lib.oracle_mttkrp.argtypes
             lib.oracle_gram.argtypes = [_D, C.c_int64, C.c_int, _D]
             lib.oracle_hadamard_grams.argtypes = [C.POINTER(_D), C.c_int, C.c_int, C.c_int, _D]
             lib.oracle_norm_sq.argtypes = [_D, C.c_int64]
@@ -155,6 +156,21 @@ def objective_explicit(T, factors) -> float:
     F = [_f64(A) for A in factors]
     d, dp = _dims(T)
     return float(lib.oracle_objective_explicit(T.ndim, dp, _ptr(T), _ptr_array(F), F[0].shape[1]))
+
+
+def cp_gradient(T, factors, mode: int) -> np.ndarray:
+    """Gradient of ``(1/2)||T - [[A]]||_F^2`` with respect to factor ``mode``:
+    the MTTKRP of the explicitly formed residual ``X - T`` (Sec. 2, eq. def:grad)."""
+    lib = _load()
+    T = _f64(T)
+    F = [_f64(A) for A in factors]
+    r = F[0].shape[1]
+    d, dp = _dims(T)
+    g = np.zeros((T.shape[mode], r))
+    rc = lib.oracle_cp_gradient(T.ndim, dp, _ptr(T), _ptr_array(F), r, mode, _ptr(g))
+    if rc:
+        raise ValueError("oracle_cp_gradient: bad arguments")
+    return g
 
 
 def objective_identity(tnorm_sq: float, M, A, V) -> float:

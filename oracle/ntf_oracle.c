@@ -189,6 +189,31 @@ double oracle_objective_explicit(int order, const int64_t* dims, const double* T
     return s;
 }
 
+/* Gradient of (1/2)||T - X||^2 with respect to factor `mode` (Sec. 2, eq.
+ * def:grad): (A_n (B^n)^T - T_[n]) B^n = (X - T)_[n] B^n, i.e. the MTTKRP of
+ * the residual tensor X - T, which is formed entrywise here. */
+int oracle_cp_gradient(int order, const int64_t* dims, const double* T, const double* const* A, int r,
+                       int mode, double* out) {
+    if (check_shape(order, dims, r) || mode < 0 || mode >= order) return 1;
+    const int64_t total = numel_of(order, dims);
+    double* R = (double*)malloc(sizeof(double) * (size_t)total);
+    if (!R) return 2;
+    int64_t idx[MAXORD] = {0};
+    for (int64_t lin = 0; lin < total; ++lin) {
+        double x = 0.0;
+        for (int p = 0; p < r; ++p) {
+            double prod = 1.0;
+            for (int l = 0; l < order; ++l) prod *= A[l][idx[l] * r + p];
+            x += prod;
+        }
+        R[lin] = x - T[lin];
+        odometer_next(order, dims, idx);
+    }
+    const int rc = oracle_mttkrp(order, dims, R, A, r, mode, out);
+    free(R);
+    return rc;
+}
+
 /* ||T - X||^2 = ||T||^2 - 2 <M_n, A_n> + sum_{pq} (V_n (*) A_n^T A_n)_{pq}:
  * the expansion that lets the restart test reuse the last block update's
  * MTTKRP and Gram product (Sec. 3.1, restart mechanism; cost I_N r^{N-1}). */

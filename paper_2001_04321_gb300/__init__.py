@@ -17,7 +17,7 @@ from typing import List, Optional, Sequence
 
 __all__ = [
     "NTFError", "lib", "load", "Opts", "Report", "mttkrp", "mttkrp_workspace_bytes", "gram",
-    "hadamard_grams", "bcd_update", "her_extrapolate", "objective", "residual_sq", "tensor_norm_sq",
+    "hadamard_grams", "bcd_update", "her_extrapolate", "block_gradient", "CPLoss", "cp_loss", "objective", "residual_sq", "tensor_norm_sq",
     "to_bf16", "her_state_init", "her_step", "solve", "solve_host", "Solver", "launch_count",
     "device_status", "HER_STATE_BYTES",
 ]
@@ -84,6 +84,7 @@ _SIGS = {
     "ntf_bcd_update": (C.c_int, [C.c_int, _P, C.c_int64, C.c_int, _P, _P, C.c_int, C.c_double, _P, C.c_size_t,
                                  _P]),
     "ntf_her_extrapolate": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P]),
+    "ntf_block_gradient": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P, _P, C.c_double, _P, _P]),
     "ntf_objective": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, _P, _P, _P]),
     "ntf_residual_workspace_bytes": (C.c_size_t, [C.POINTER(_Tensor), C.c_int]),
     "ntf_residual_sq": (C.c_int, [C.POINTER(_Tensor), C.POINTER(_P), C.c_int, _P, _P, C.c_size_t, _P]),
@@ -264,6 +265,20 @@ def bcd_update(A, M, V, method: str = "hals", inner_max: int = 1, inner_tol: flo
     _check(load().ntf_bcd_update(m, _ptr(A), rows, r, _ptr(M), _ptr(V), inner_max, inner_tol, _ptr(workspace),
                                  workspace.numel(), _stream(stream)))
     return A
+
+
+def block_gradient(A, M, V, scale: float = 1.0, scale_dev=None, out=None, stream=None):
+    """``scale * (A V - M)``: gradient of (1/2)||T - X||^2 with respect to ``A``."""
+    torch = _torch()
+    _require_cuda(A, "A", torch.float32)
+    _require_cuda(M, "M", torch.float32)
+    _require_cuda(V, "V", torch.float64)
+    if out is None:
+        out = torch.empty_like(A)
+    _check(load().ntf_block_gradient(_ptr(A), int(A.shape[0]), int(A.shape[1]), _ptr(M), _ptr(V),
+                                     None if scale_dev is None else _ptr(scale_dev), float(scale), _ptr(out),
+                                     _stream(stream)))
+    return out
 
 
 def her_extrapolate(A, A_prev, beta_dev, out=None, stream=None):
@@ -471,3 +486,6 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+from .autograd import CPLoss, cp_loss  # noqa: E402  (re-exported)

@@ -212,6 +212,21 @@ ntf_status ntf_bcd_update(ntf_method method, float* A, int64_t rows, int rank, c
     return NTF_OK;
 }
 
+ntf_status ntf_block_gradient(const float* A, int64_t rows, int rank, const float* M, const double* V,
+                              const double* scale_dev, double scale, float* out, void* stream) {
+    NTF_TRY(check_rank(rank));
+    if (rows < 1) return fail(NTF_EINVAL, "rows must be >= 1");
+    NTF_TRY(check_device_ptr(A, "A"));
+    NTF_TRY(check_device_ptr(M, "M"));
+    NTF_TRY(check_device_ptr(V, "V"));
+    NTF_TRY(check_device_ptr(out, "out"));
+    if (scale_dev) NTF_TRY(check_device_ptr(scale_dev, "scale_dev"));
+    cudaError_t e = launch_block_gradient(A, rows, rank, M, V, scale_dev, scale, out,
+                                          static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "ntf_block_gradient");
+    return NTF_OK;
+}
+
 ntf_status ntf_her_extrapolate(const float* A, const float* A_prev, const double* beta_dev, int64_t n, float* A_hat,
                                void* stream) {
     if (n < 1) return fail(NTF_EINVAL, "n must be >= 1");

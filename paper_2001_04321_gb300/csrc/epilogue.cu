@@ -42,20 +42,21 @@ __device__ __forceinline__ double warp_sum_dd(double v) {
     return v;
 }
 
-// FP64 sum of the epilogue CTAs' FP32 partial Gram entry q (k = 0: A, 1: A_hat), in
-// groups of eight independent loads added as a tree (fixed order)
+// FP64 sum of the epilogue CTAs' FP32 partial Gram entry q (k = 0: A, 1: A_hat):
+// 16 independent loads in flight, added in a fixed order
 __device__ __forceinline__ double sum_gram_partials(const float* gpart, int nblk, int rr, int k, int q) {
     double s = 0.0;
     const float* base = gpart + (int64_t)k * rr + q;
     const int64_t stride = 2 * (int64_t)rr;
-    int b = 0;
-    for (; b + 8 <= nblk; b += 8) {
-        float x[8];
+    for (int b = 0; b < nblk; b += 16) {
+        float x[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = base[(b + u) * stride];
-        s += (((double)x[0] + x[1]) + ((double)x[2] + x[3])) + (((double)x[4] + x[5]) + ((double)x[6] + x[7]));
+        for (int u = 0; u < 16; ++u) x[u] = (b + u < nblk) ? base[(int64_t)(b + u) * stride] : 0.f;
+        double t = 0.0;
+#pragma unroll
+        for (int u = 0; u < 16; u += 2) t += (double)x[u] + (double)x[u + 1];
+        s += t;
     }
-    for (; b < nblk; ++b) s += (double)base[b * stride];
     return s;
 }
 

@@ -34,10 +34,26 @@ __device__ __forceinline__ float reduce_inner(const ReduceParams& P, int64_t j, 
     const int64_t slot = (int64_t)P.part_warps * P.I_T * P.RP;          // one (CTA, segment) slot
     const float* q = P.part + (int64_t)b * P.RP + p;
     float s = 0.f;
+    if (P.part_warps == 1) {
+        // one partial per CTA: up to 16 independent loads in flight, summed in order
+        s = q[((int64_t)g0 * P.Smax + seg0) * slot];
+        for (int g = g0 + 1; g <= g1; g += 16) {
+            float x[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) x[u] = (g + u <= g1) ? q[((int64_t)(g + u) * P.Smax) * slot] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) s += x[u];
+        }
+        return s;
+    }
     for (int w = 0; w < P.part_warps; ++w) s += q[((int64_t)g0 * P.Smax + seg0) * slot + (int64_t)w * P.I_T * P.RP];
-#pragma unroll 8
-    for (int g = g0 + 1; g <= g1; ++g)
-        for (int w = 0; w < P.part_warps; ++w) s += q[((int64_t)g * P.Smax) * slot + (int64_t)w * P.I_T * P.RP];
+    for (int g = g0 + 1; g <= g1; ++g) {
+        float x[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) x[w] = w < P.part_warps ? q[((int64_t)g * P.Smax) * slot + (int64_t)w * P.I_T * P.RP] : 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s += x[w];
+    }
     return s;
 }
 
@@ -59,8 +75,15 @@ __device__ __forceinline__ float reduce_outer(const ReduceParams& P, int64_t j, 
 // Last mode: one partial per streaming CTA along the tile axis.
 __device__ __forceinline__ float reduce_last(const ReduceParams& P, int64_t c, int p) {
     float s = 0.f;
-#pragma unroll 8
-    for (int g = 0; g < P.G; ++g) s += P.part[((int64_t)g * P.Cpad + c) * P.RP + p];
+    const float* q = P.part + c * P.RP + p;
+    const int64_t stride = P.Cpad * P.RP;
+    for (int g = 0; g < P.G; g += 16) {
+        float x[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) x[u] = (g + u < P.G) ? q[(int64_t)(g + u) * stride] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) s += x[u];
+    }
     return s;
 }
 

@@ -362,6 +362,37 @@ cudaError_t launch_bcd(int method, float* A, int64_t rows, int r, const float* M
 }
 
 // ---------------------------------------------------------------------------
+// gradient of (1/2)||T - X||^2 with respect to one factor (Sec. 2, eq. def:grad
+// with Appendix A's Hadamard product): out = scale (A V - M), one row per thread
+// ---------------------------------------------------------------------------
+__global__ void k_block_gradient(const float* __restrict__ A, int64_t rows, int r, const float* __restrict__ M,
+                                 const double* __restrict__ V, const double* __restrict__ scale_dev, double scale,
+                                 float* __restrict__ out) {
+    __shared__ float Vs[NTF_MAX_RANK * NTF_MAX_RANK];
+    for (int q = threadIdx.x; q < r * r; q += blockDim.x) Vs[q] = (float)V[q];
+    __syncthreads();
+    const float sc = (float)(scale_dev ? *scale_dev * scale : scale);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
+        const float* a = A + i * r;
+        for (int j = 0; j < r; ++j) {
+            float g = -M[i * r + j];
+            for (int l = 0; l < r; ++l) g = fmaf(a[l], Vs[l * r + j], g);
+            out[i * r + j] = sc * g;
+        }
+    }
+}
+
+cudaError_t launch_block_gradient(const float* A, int64_t rows, int r, const float* M, const double* V,
+                                  const double* scale_dev, double scale, float* out, cudaStream_t st) {
+    int64_t g = (rows + 127) / 128;
+    if (g > 1024) g = 1024;
+    if (g < 1) g = 1;
+    k_block_gradient<<<(int)g, 128, 0, st>>>(A, rows, r, M, V, scale_dev, scale, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // a4: extrapolation  A_hat = max(0, A + beta (A - A_prev))
 // ---------------------------------------------------------------------------
 __global__ void k_extrapolate(const float* __restrict__ A, const float* __restrict__ Ap,

@@ -122,6 +122,28 @@ def test_gradient_identity_finite_difference():
         np.testing.assert_allclose(grad, fd, rtol=1e-6, atol=1e-7)
 
 
+def test_cp_gradient_matches_finite_differences_and_vanishes_at_exact_fit():
+    # oracle.cp_gradient forms X - T explicitly and applies the MTTKRP; central
+    # differences of the explicit objective pin it, and at an exact
+    # factorization (T = [[F]]) the gradient is zero.
+    T, F = rand_problem((3, 4, 2, 3), 2, 8)
+    h = 1e-6
+    for n in range(4):
+        g = oracle.cp_gradient(T, F, n)
+        fd = np.zeros_like(F[n])
+        for i in range(F[n].shape[0]):
+            for p in range(F[n].shape[1]):
+                Fp = [A.copy() for A in F]
+                Fm = [A.copy() for A in F]
+                Fp[n][i, p] += h
+                Fm[n][i, p] -= h
+                fd[i, p] = (0.5 * oracle.objective_explicit(T, Fp) - 0.5 * oracle.objective_explicit(T, Fm)) / (2 * h)
+        np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-7)
+    X = np.einsum("iz,jz,kz,lz->ijkl", *F)
+    for n in range(4):
+        assert np.abs(oracle.cp_gradient(X, F, n)).max() <= 1e-12
+
+
 # --- HALS (Sec. 2.1.4) --------------------------------------------------------
 
 def _block_problem(seed, I=6, r=3, dims_other=(5, 4)):
