@@ -20,6 +20,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -100,8 +101,7 @@ def whole_job_rate(units_per_rank: int, ms_local: float, ws: int):
 class ClockSampler:
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                 f".clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"ntf_clocks_{os.getpid()}_{gpu_index}.csv")
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={CLOCK_FIELDS}",
@@ -315,7 +315,7 @@ def gpu_arm(args):
                    "storage": "bf16 tensor (cast once, RNE), fp32 factors and accumulation, fp64 objective/restart",
                    "l2": "inputs larger than L2 (250 MB bf16 / 500 MB fp32 tensor): no flush",
                    "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "hbm", "kernel": "MTTKRP streaming kernel (k_stream_rows / k_stream_last)",
+        "roofline": {"bound": "hbm", "kernel": "MTTKRP tensor-core streams k_tc_rows / k_tc_last (tcgen05, TMA)",
                      "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs (copy)",

@@ -256,7 +256,7 @@ def solve(T, init, iters: int, her: bool = True, method: str = "hals", inner_max
           track_blocks: bool = False):
     """Alg. 1 (``her=False``) or Alg. 2 (``her=True``) in FP64 from ``init``.
 
-    Returns ``(factors, trace)``; ``trace.fhat[k-1]`` is F-hat_k (Alg. 2 line 9),
+    Returns ``(factors, trace)``; ``trace.fhat[k-1]`` is F-hat_k (the value Alg. 2's restart test compares),
     ``trace.ftrue[k-1]`` the explicit objective at A_k when ``track_true``.
     """
     lib = _load()

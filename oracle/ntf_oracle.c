@@ -399,7 +399,7 @@ int oracle_her_decide(double* state, double f_hat, double gamma, double gamma_ba
 /* method: 0 = HALS, 1 = projected gradient.
  * Outputs (each may be NULL), one entry per outer iteration k = 1..max_iters:
  *   out_fhat[k-1]     F-hat_k = ||T - [[A_hat^1..A_hat^{N-1}, A^N]]||^2 by the
- *                     identity from the last block's MTTKRP (Alg. 2, line 9);
+ *                     identity from the last block's MTTKRP (Alg. 2, restart test);
  *   out_beta[k-1], out_beta_bar[k-1], out_restart[k-1]  after the decision;
  *   out_ftrue[k-1]    ||T - [[A_k]]||^2 explicitly (eq. err_true_def, times 2);
  *   out_fblock[(k-1)N + i]  ||T - X||^2 right after block i's update, explicit
@@ -455,7 +455,7 @@ int oracle_solve(int order, const int64_t* dims, const double* T, double* const*
                     oracle_objective_explicit(order, dims, T, (const double* const*)A, r);
         }
         /* F-hat_k = F(A_hat^1..A_hat^{N-1}, A^N): M and V of the last block
-         * were formed against exactly those A_hat (Alg. 2, line 9). */
+         * were formed against exactly those A_hat (Alg. 2, restart test). */
         const int last = order - 1;
         const double fhat = oracle_objective_identity(tnorm, M[last], A[last], dims[last], r, V);
         int restart = 0;

@@ -13,11 +13,14 @@
 //               the Grams of A and A_hat, of <M, A> and (last mode) of
 //               sum(V (*) A^T A);
 //
-// and once per iteration
+// and, in the CTA of the last mode's epilogue that finishes last, the end of
+// the iteration: F_hat = ||T||^2 - 2<M,A> + sum(V (*) A^T A) from those
+// partials (Sec. 3.1, a5), the restart decision of Alg. 2 (a6), and the
+// accept/restart step as a flip of the current-buffer indices.
 //
-//   k_finish    F_hat = ||T||^2 - 2<M,A> + sum(V (*) A^T A) from those partials
-//               (Sec. 3.1, a5), the restart decision of Alg. 2 (a6), and the
-//               accept/restart step as a flip of the current-buffer indices.
+// GB300 runs FP64 at a small fraction of its FP32 rate (a dependent FP64 add
+// costs about 70 cycles), so the per-entry sums here are FP32 butterflies in a
+// fixed order, and FP64 is kept for the few scalars where cancellation matters.
 //
 // The HALS sweep keeps the residual g = M - A V of the row in the lanes (lane
 // p holds column p): updating column j is one scalar step on lane j followed
@@ -42,22 +45,23 @@ __device__ __forceinline__ double warp_sum_dd(double v) {
     return v;
 }
 
-// FP64 sum of the epilogue CTAs' FP32 partial Gram entry q (k = 0: A, 1: A_hat):
-// 16 independent loads in flight, added in a fixed order
-__device__ __forceinline__ double sum_gram_partials(const float* gpart, int nblk, int rr, int k, int q) {
-    double s = 0.0;
+// butterfly sum over the lanes: every lane ends with the same value
+__device__ __forceinline__ float warp_allsum_f(float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Gram entry q (k = 0: A, 1: A_hat) from the epilogue CTAs' partials: lane u adds
+// the partials of CTAs u, u + 32, ... in order, then a butterfly over the lanes.
+// Every entry of a Gram of nonnegative factors is a sum of nonnegative terms,
+// so FP32 summation keeps a relative error of a few units in the last place.
+__device__ __forceinline__ float gram_entry(const float* gpart, int nblk, int rr, int k, int q, int lane) {
     const float* base = gpart + (int64_t)k * rr + q;
     const int64_t stride = 2 * (int64_t)rr;
-    for (int b = 0; b < nblk; b += 16) {
-        float x[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) x[u] = (b + u < nblk) ? base[(int64_t)(b + u) * stride] : 0.f;
-        double t = 0.0;
-#pragma unroll
-        for (int u = 0; u < 16; u += 2) t += (double)x[u] + (double)x[u + 1];
-        s += t;
-    }
-    return s;
+    float s = 0.f;
+    for (int b = lane; b < nblk; b += 32) s += base[(int64_t)b * stride];
+    return warp_allsum_f(s);
 }
 
 // pairing factor A_hat_l as seen by the update of mode n (eq. NNLS_her_exact):
@@ -83,39 +87,40 @@ __global__ void k_prep(const PrepParams P) {
     const bool fin = P.fin_mode >= 0 && (!end_of_iter || *B.iters > 0);
     const bool two = fin && !end_of_iter && B.her;     // mid-iteration with HER: Grams of A and A_hat
     const int nVG = rr * (two ? 2 : 1);
-    // (1) V and the finished Grams: items spread over the blocks
-    for (int i = blockIdx.x + gridDim.x * threadIdx.x; i < nVG; i += gridDim.x * blockDim.x) {
-        const int q = i % rr;
-        if (i >= rr) {
-            // Gram of A_{n-1} (not extrapolated): only stored
-            const int f = P.fin_mode, c = B.cur[f];
-            B.GB[f][c][q] = sum_gram_partials(P.gpart, P.fin_blocks, rr, 0, q);
-            continue;
+    // (1) the finished Grams of fin_mode and V_n: one warp per entry q, the
+    // warps of different blocks first
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int keep = (end_of_iter && B.her && P.her && P.her->last_restart == 0) ? 1 : 0;
+    for (int q = blockIdx.x + gridDim.x * warp; q < rr; q += nwarps) {
+        float sA = 0.f, sH = 0.f;
+        if (fin) {
+            sA = gram_entry(P.gpart, P.fin_blocks, rr, end_of_iter ? keep : 0, q, lane);
+            if (two) sH = gram_entry(P.gpart, P.fin_blocks, rr, 1, q, lane);
         }
-        double v = 1.0;
-        for (int l = 0; l < P.order; ++l) {
-            if (l == n) continue;
-            double gl;
-            if (fin && l == P.fin_mode) {
-                const int c = B.cur[l];
-                if (end_of_iter) {
-                    // previous iteration's last mode: the kept factor (A on restart, A_hat on accept)
-                    const int k = (B.her && P.her && P.her->last_restart == 0) ? 1 : 0;
-                    gl = sum_gram_partials(P.gpart, P.fin_blocks, rr, k, q);
-                    B.GB[l][c][q] = gl;
-                } else if (B.her) {
-                    gl = sum_gram_partials(P.gpart, P.fin_blocks, rr, 1, q);   // A_hat_{n-1}
-                    B.GB[l][1 - c][q] = gl;
+        if (lane == 0) {
+            double v = 1.0;
+            for (int l = 0; l < P.order; ++l) {
+                if (l == n) continue;
+                double gl;
+                if (fin && l == P.fin_mode) {
+                    const int c = B.cur[l];
+                    // end of iteration: the kept factor (A on restart, A_hat on accept), already current;
+                    // mid-iteration with HER: A_{n-1} is stored, A_hat_{n-1} pairs with mode n
+                    B.GB[l][c][q] = (double)sA;
+                    gl = (double)sA;
+                    if (two) {
+                        gl = (double)sH;
+                        B.GB[l][1 - c][q] = gl;
+                    }
                 } else {
-                    gl = sum_gram_partials(P.gpart, P.fin_blocks, rr, 0, q);
-                    B.GB[l][c][q] = gl;
+                    gl = pairing_gram(B, l, n)[q];
                 }
-            } else {
-                gl = pairing_gram(B, l, n)[q];
+                v *= gl;
             }
-            v *= gl;
+            P.V[q] = v;
+            P.Vf[q] = (float)v;
         }
-        P.V[q] = v;
     }
     // (2) packed factors and weights
     const int64_t nFc = P.Fc ? P.Fc_rows_out * P.RP : P.FcT ? (int64_t)P.n_kc * 2 * P.RPH * 64 : 0;
@@ -175,7 +180,7 @@ __global__ void k_prep(const PrepParams P) {
 }
 
 cudaError_t launch_prep(const PrepParams& P, cudaStream_t st) {
-    const int64_t total = (int64_t)2 * P.r * P.r +
+    const int64_t total = (int64_t)32 * P.r * P.r +
                           (P.Fc ? P.Fc_rows_out * P.RP : P.FcT ? (int64_t)P.n_kc * 2 * P.RPH * 64 : 0) +
                           (P.Fi ? P.Ii * P.RP : 0) + (P.W ? P.n_o * P.RP : 0);
     int64_t g = (total + 255) / 256;
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) 
     float* Ah = her ? P.B.X[n][1 - cn] : nullptr; // out: A_hat_k
     for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
         const int l = q >> 5, c = q & 31;
-        Vs[l * 33 + c] = (l < r && c < r) ? (float)P.V[l * r + c] : 0.f;
+        Vs[l * 33 + c] = (l < r && c < r) ? P.Vf[l * r + c] : 0.f;
     }
     const float beta = her ? (float)*P.beta : 0.f;
 
@@ -286,85 +291,76 @@ __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) 
         }
         P.gpart[((int64_t)blockIdx.x * 2 + 0) * rr + q] = sa;
         if (her) P.gpart[((int64_t)blockIdx.x * 2 + 1) * rr + q] = sh;
-        if (P.last) quad += P.V[q] * (double)sa;
+        if (P.last) quad = fma(P.V[q], (double)sa, quad);
     }
     if (P.last) {
         quad = warp_sum_dd(quad);
         if (lane == 0) dred[warp] = quad;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0, qs = 0.0;
-        for (int w = 0; w < kEpiWarps; ++w) s += (double)winner[w];
-        P.ipart[blockIdx.x] = s;
-        if (P.last) {
-            for (int w = 0; w < kEpiWarps; ++w) qs += dred[w];
-            P.qpart[blockIdx.x] = qs;
+    if (warp == 0) {
+        // the CTA's sums over its 8 warps: 3-level butterflies on lanes 0..7
+        double s = lane < kEpiWarps ? (double)winner[lane] : 0.0;
+        double qs = (P.last && lane < kEpiWarps) ? dred[lane] : 0.0;
+#pragma unroll
+        for (int off = kEpiWarps / 2; off > 0; off >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, off);
+            qs += __shfl_xor_sync(0xffffffffu, qs, off);
+        }
+        if (lane == 0) {
+            P.ipart[blockIdx.x] = s;
+            if (P.last) P.qpart[blockIdx.x] = qs;
         }
     }
+    if (!P.last) return;
+
+    // end of the iteration, in the CTA that finishes last (its partials and every
+    // other CTA's are visible after the fence / counter handshake)
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(P.ticket, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!is_last || warp != 0) return;
+    __threadfence();
+    double isum = 0.0, qsum = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+        isum += __ldcg(P.ipart + b);
+        qsum += __ldcg(P.qpart + b);
+    }
+    isum = warp_sum_dd(isum);
+    qsum = warp_sum_dd(qsum);
+    if (lane != 0) return;
+    *P.ticket = 0;
+    const double fhat = *P.tnorm - 2.0 * isum + qsum;
+    *P.fhat_out = fhat;
+    *P.iters_out += 1;
+    if (!P.her) return;
+    // Alg. 2: restart if F_hat_k > F_hat_{k-1}; a non-finite F_hat restarts and is flagged
+    ntf_her_state* hs = P.her;
+    const double b0 = hs->beta, bb = hs->beta_bar;
+    const bool finite = isfinite(fhat);
+    const int restart = (!finite || fhat > hs->f_hat_prev) ? 1 : 0;
+    if (restart) {
+        hs->beta_bar = b0;
+        hs->beta = b0 / hs->eta;
+    } else {
+        hs->beta_bar = fmin(1.0, hs->gamma_bar * bb);
+        hs->beta = fmin(bb, hs->gamma * b0);
+        // keep the extrapolated sequence: A_k <- A_hat_k for every block
+        for (int l = 0; l < P.order; ++l) P.B.cur[l] = 1 - P.B.cur[l];
+    }
+    hs->f_hat_prev = fhat;
+    hs->iters += 1;
+    hs->restarts += restart;
+    hs->last_restart = restart;
+    if (!finite) hs->numeric_error = 1;
 }
 
 int epilogue_blocks(int64_t rows) { return (int)((rows + kEpiRows - 1) / kEpiRows); }
 
 cudaError_t launch_epilogue(const EpiParams& P, cudaStream_t st) {
     k_epilogue<<<epilogue_blocks(P.rows), kEpiWarps * 32, 0, st>>>(P);
-    count_launch();
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// end of an iteration: F_hat, the restart decision, the buffer flip
-// ---------------------------------------------------------------------------
-constexpr int kFinishThreads = 256;
-
-__global__ void __launch_bounds__(kFinishThreads) k_finish(const FinishParams P) {
-    __shared__ double sred[2][kFinishThreads / 32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double inner = 0.0, quad = 0.0;
-    for (int b = threadIdx.x; b < P.blocks; b += blockDim.x) {
-        inner += P.ipart[b];
-        quad += P.qpart[b];
-    }
-    inner = warp_sum_dd(inner);
-    quad = warp_sum_dd(quad);
-    if (lane == 0) {
-        sred[0][warp] = inner;
-        sred[1][warp] = quad;
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    double isum = 0.0, qsum = 0.0;
-    for (int w = 0; w < kFinishThreads / 32; ++w) {
-        isum += sred[0][w];
-        qsum += sred[1][w];
-    }
-    const double fhat = *P.tnorm - 2.0 * isum + qsum;
-    *P.fhat_out = fhat;
-    *P.iters_out += 1;
-    if (!P.her) return;
-    // Alg. 2: restart if F_hat_k > F_hat_{k-1}; a non-finite F_hat restarts and is flagged
-    ntf_her_state* s = P.her;
-    const double b0 = s->beta, bb = s->beta_bar;
-    const bool finite = isfinite(fhat);
-    const int restart = (!finite || fhat > s->f_hat_prev) ? 1 : 0;
-    if (restart) {
-        s->beta_bar = b0;
-        s->beta = b0 / s->eta;
-    } else {
-        s->beta_bar = fmin(1.0, s->gamma_bar * bb);
-        s->beta = fmin(bb, s->gamma * b0);
-        // keep the extrapolated sequence: A_k <- A_hat_k for every block
-        for (int l = 0; l < P.order; ++l) P.B.cur[l] = 1 - P.B.cur[l];
-    }
-    s->f_hat_prev = fhat;
-    s->iters += 1;
-    s->restarts += restart;
-    s->last_restart = restart;
-    if (!finite) s->numeric_error = 1;
-}
-
-cudaError_t launch_finish(const FinishParams& P, cudaStream_t st) {
-    k_finish<<<1, kFinishThreads, 0, st>>>(P);
     count_launch();
     return cudaGetLastError();
 }

@@ -25,6 +25,7 @@ struct PrepParams {
     int64_t C, Ii, n_o, Fc_rows_out;
     int64_t dims[NTF_MAX_ORDER];
     double* V;                          // r x r
+    float* Vf;                          // r x r, V rounded to FP32 (read by the epilogue's HALS sweep)
     float* Fc;                          // packed last-mode factor (FFMA stream), or nullptr
     __nv_bfloat16* FcT;                 // tensor-core operand (64-row chunks, bf16 hi|lo), or nullptr
     int fct_mode;                       // mode packed into FcT
@@ -42,23 +43,20 @@ struct PrepParams {
 struct EpiParams {
     FusedBufs B;
     ReduceParams red;
-    int mode;
+    int mode, order;
     int64_t rows;
     int r;
-    int last;              // 1 for mode N-1: also partial sum(V (*) G(A))
+    int last;              // 1 for mode N-1: also partial sum(V (*) G(A)), then the end of the iteration
     const double* beta;    // device beta_{k-1}
     const double* V;       // r x r
+    const float* Vf;       // r x r, FP32
     float* gpart;          // [blocks][2][r*r]: partial Grams of A and A_hat
     double* ipart;         // [blocks]: partial <M, A>
     double* qpart;         // [blocks]: partial sum(V (*) G(A)) (last mode)
-};
-
-struct FinishParams {
-    FusedBufs B;
-    int order, blocks;     // blocks: epilogue CTAs of the last mode
-    const double* ipart;
-    const double* qpart;
-    const double* tnorm;
+    // end of the iteration (last mode only), taken by the CTA that finishes last:
+    // F_hat, the restart decision of Alg. 2 and the buffer flip
+    int* ticket;           // device counter, 0 between launches
+    const double* tnorm;   // ||T||^2
     double* fhat_out;
     int* iters_out;        // outer-iteration counter
     ntf_her_state* her;    // nullptr without HER
@@ -66,7 +64,6 @@ struct FinishParams {
 
 cudaError_t launch_prep(const PrepParams& P, cudaStream_t st);
 cudaError_t launch_epilogue(const EpiParams& P, cudaStream_t st);
-cudaError_t launch_finish(const FinishParams& P, cudaStream_t st);
 int epilogue_blocks(int64_t rows);
 
 // streaming kernel of a plan alone (the packed factors / W already in place)

@@ -468,31 +468,61 @@ cudaError_t launch_objective(const double* tn, const float* M, const float* A, i
 // ---------------------------------------------------------------------------
 constexpr int kStreamRedThreads = 256;
 
+// 16-byte vector of the stored type, unpacked to FP32 (bf16 -> f32 is exact)
 template <typename TE>
-__device__ __forceinline__ float load_elem(const TE* p);
+struct Vec16;
 template <>
-__device__ __forceinline__ float load_elem<float>(const float* p) { return __ldg(p); }
+struct Vec16<float> {
+    static constexpr int n = 4;
+    __device__ __forceinline__ static void unpack(const uint4& u, float* x) {
+        x[0] = __uint_as_float(u.x);
+        x[1] = __uint_as_float(u.y);
+        x[2] = __uint_as_float(u.z);
+        x[3] = __uint_as_float(u.w);
+    }
+};
 template <>
-__device__ __forceinline__ float load_elem<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+struct Vec16<__nv_bfloat16> {
+    static constexpr int n = 8;
+    __device__ __forceinline__ static void unpack(const uint4& u, float* x) {
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            x[2 * k] = __uint_as_float(w[k] << 16);
+            x[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+    }
+};
 
+// ||T||^2: warp per row, 16-byte loads, four per lane in flight; the padding
+// between C and ld is never summed
 template <typename TE>
 __global__ void __launch_bounds__(kStreamRedThreads) k_norm_sq(const TE* __restrict__ T, int64_t rows, int64_t C,
                                                                int64_t ld, double* __restrict__ parts) {
     __shared__ double sbuf[33];
+    constexpr int E = Vec16<TE>::n;
     const int lane = threadIdx.x & 31;
     const int64_t warp_g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nv = (C + E - 1) / E;          // 16-byte vectors holding the row's C values
     double acc = 0.0;
     for (int64_t row = warp_g; row < rows; row += nwarps) {
-        const TE* rp = T + row * ld;
-        float s = 0.f;
-        int cnt = 0;
-        for (int64_t c = lane; c < C; c += 32) {
-            const float v = load_elem<TE>(rp + c);
-            s = fmaf(v, v, s);
-            if (++cnt == 64) { acc += (double)s; s = 0.f; cnt = 0; }
+        const uint4* rp = reinterpret_cast<const uint4*>(T + row * ld);
+        for (int64_t v0 = lane; v0 < nv; v0 += 128) {
+            uint4 u[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) u[k] = (v0 + 32 * k < nv) ? __ldg(rp + v0 + 32 * k) : make_uint4(0, 0, 0, 0);
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float x[E];
+                Vec16<TE>::unpack(u[k], x);
+                const int64_t c0 = (v0 + 32 * k) * E;
+#pragma unroll
+                for (int j = 0; j < E; ++j) s = (c0 + j < C) ? fmaf(x[j], x[j], s) : s;
+            }
+            acc += (double)s;
         }
-        acc += (double)s;
     }
     const double tot = block_sum_d(acc, sbuf);
     if (threadIdx.x == 0) parts[blockIdx.x] = tot;
@@ -506,7 +536,7 @@ __global__ void k_sum_parts(const double* __restrict__ parts, int n, double* __r
     if (threadIdx.x == 0) *out = acc;
 }
 
-int stream_red_blocks() { return 2 * num_sms(); }
+int stream_red_blocks() { return 4 * num_sms(); }
 
 cudaError_t launch_norm_sq(const TensorView& v, double* parts, double* out, cudaStream_t st) {
     const int G = stream_red_blocks();
@@ -522,37 +552,104 @@ cudaError_t launch_norm_sq(const TensorView& v, double* parts, double* out, cuda
     return cudaGetLastError();
 }
 
-// residual: warp per row (o, i); KR row = W(o,:) * A_{N-2}(i,:) in shared memory
+// Explicit residual ||T - X||^2 with X(o, i, c) = sum_p W(o,p) A_{N-2}(i,p) A_{N-1}(c,p).
+// A CTA takes blocks of 64 rows (o, i); per chunk of CW columns A_{N-1}^T is staged
+// in shared memory, and each lane computes a 4-row x 4-column tile of X (16 FMAs
+// per p from one float4 of A_{N-1}^T and one broadcast float4 of the 4 rows'
+// Khatri-Rao values), after its 4 x 4 tensor values are already in registers.
+constexpr int kResRowsPerWarp = 4;
+constexpr int kResGroups = 2;                                    // row groups per warp per chunk
+constexpr int kResRows = (kStreamRedThreads / 32) * kResRowsPerWarp * kResGroups;   // 64 rows per block
+
+int residual_chunk(int r) { return r <= 16 ? 512 : r <= 32 ? 256 : 128; }   // r * CW * 4 <= 32 KB
+
+template <typename TE>
+__device__ __forceinline__ void load4(const TE* p, float* x);
+template <>
+__device__ __forceinline__ void load4<float>(const float* p, float* x) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load4<__nv_bfloat16>(const __nv_bfloat16* p, float* x) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+    x[0] = __uint_as_float(v.x << 16), x[1] = __uint_as_float(v.x & 0xffff0000u);
+    x[2] = __uint_as_float(v.y << 16), x[3] = __uint_as_float(v.y & 0xffff0000u);
+}
+
 template <typename TE>
 __global__ void __launch_bounds__(kStreamRedThreads) k_residual_sq(const TE* __restrict__ T, int64_t Ii, int64_t n_o,
-                                                                   int64_t C, int64_t ld, int r,
+                                                                   int64_t C, int64_t ld, int r, int CW,
                                                                    const float* __restrict__ W, int RP,
                                                                    const float* __restrict__ Ai,
                                                                    const float* __restrict__ Ac,
                                                                    double* __restrict__ parts) {
+    extern __shared__ __align__(16) float AcT[];                 // [r][CW]
+    __shared__ __align__(16) float krT[kStreamRedThreads / 32][NTF_MAX_RANK][kResRowsPerWarp];
     __shared__ double sbuf[33];
-    __shared__ float kr_s[kStreamRedThreads / 32][NTF_MAX_RANK];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int64_t warp_g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t rows = Ii * n_o;
+    const int64_t nblk = (rows + kResRows - 1) / kResRows;
     double acc = 0.0;
-    for (int64_t row = warp_g; row < rows; row += nwarps) {
-        const int64_t o = row / Ii, i = row % Ii;
-        __syncwarp();
-        for (int p = lane; p < r; p += 32) kr_s[wl][p] = W[o * RP + p] * Ai[i * r + p];
-        __syncwarp();
-        const TE* rp = T + row * ld;
-        float s = 0.f;
-        int cnt = 0;
-        for (int64_t c = lane; c < C; c += 32) {
-            float x = 0.f;
-            for (int p = 0; p < r; ++p) x = fmaf(kr_s[wl][p], __ldg(Ac + c * r + p), x);
-            const float d = load_elem<TE>(rp + c) - x;
-            s = fmaf(d, d, s);
-            if (++cnt == 64) { acc += (double)s; s = 0.f; cnt = 0; }
+    for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+        for (int64_t cb = 0; cb < C; cb += CW) {
+            const int cw = (int)min((int64_t)CW, C - cb);
+            __syncthreads();
+            for (int q = threadIdx.x; q < r * CW; q += blockDim.x) {
+                const int p = q / CW, c = q - p * CW;
+                AcT[q] = c < cw ? Ac[(cb + c) * r + p] : 0.f;
+            }
+            __syncthreads();
+            for (int g = 0; g < kResGroups; ++g) {
+                const int64_t row0 = blk * kResRows + (int64_t)(g * (kStreamRedThreads / 32) + wl) * kResRowsPerWarp;
+                if (row0 >= rows) continue;                        // warp-uniform
+                __syncwarp();
+                for (int p = lane; p < r; p += 32)
+#pragma unroll
+                    for (int k = 0; k < kResRowsPerWarp; ++k) {
+                        const int64_t row = row0 + k;
+                        float kr = 0.f;
+                        if (row < rows) {
+                            const int64_t o = row / Ii, i = row - o * Ii;
+                            kr = W[o * RP + p] * Ai[i * r + p];
+                        }
+                        krT[wl][p][k] = kr;
+                    }
+                __syncwarp();
+                for (int c0 = 4 * lane; c0 < cw; c0 += 128) {
+                    float t[kResRowsPerWarp][4];
+#pragma unroll
+                    for (int k = 0; k < kResRowsPerWarp; ++k) {
+                        if (row0 + k < rows) load4<TE>(T + (row0 + k) * ld + cb + c0, t[k]);
+                        else t[k][0] = t[k][1] = t[k][2] = t[k][3] = 0.f;
+                    }
+                    float x[kResRowsPerWarp][4];
+#pragma unroll
+                    for (int k = 0; k < kResRowsPerWarp; ++k) x[k][0] = x[k][1] = x[k][2] = x[k][3] = 0.f;
+                    for (int p = 0; p < r; ++p) {
+                        const float4 a = *reinterpret_cast<const float4*>(&AcT[p * CW + c0]);
+                        const float4 kk = *reinterpret_cast<const float4*>(&krT[wl][p][0]);
+                        const float kv[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+                        for (int k = 0; k < kResRowsPerWarp; ++k) {
+                            x[k][0] = fmaf(kv[k], a.x, x[k][0]);
+                            x[k][1] = fmaf(kv[k], a.y, x[k][1]);
+                            x[k][2] = fmaf(kv[k], a.z, x[k][2]);
+                            x[k][3] = fmaf(kv[k], a.w, x[k][3]);
+                        }
+                    }
+                    float s = 0.f;
+#pragma unroll
+                    for (int k = 0; k < kResRowsPerWarp; ++k)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float d = t[k][j] - x[k][j];
+                            s = (row0 + k < rows && c0 + j < cw) ? fmaf(d, d, s) : s;
+                        }
+                    acc += (double)s;
+                }
+            }
         }
-        acc += (double)s;
     }
     const double tot = block_sum_d(acc, sbuf);
     if (threadIdx.x == 0) parts[blockIdx.x] = tot;
@@ -560,13 +657,16 @@ __global__ void __launch_bounds__(kStreamRedThreads) k_residual_sq(const TE* __r
 
 cudaError_t launch_residual_sq(const TensorView& v, int r, const float* W, int RP, const float* Ai, const float* Ac,
                                double* parts, double* out, cudaStream_t st) {
-    const int G = stream_red_blocks();
+    const int64_t nblk = (v.Ii * v.n_o + kResRows - 1) / kResRows;
+    const int G = (int)std::min<int64_t>(nblk, stream_red_blocks());
+    const int CW = residual_chunk(r);
+    const size_t smem = sizeof(float) * (size_t)r * CW;
     if (v.dtype == NTF_F32)
-        k_residual_sq<float><<<G, kStreamRedThreads, 0, st>>>(static_cast<const float*>(v.data), v.Ii, v.n_o, v.C,
-                                                              v.ld, r, W, RP, Ai, Ac, parts);
+        k_residual_sq<float><<<G, kStreamRedThreads, smem, st>>>(static_cast<const float*>(v.data), v.Ii, v.n_o, v.C,
+                                                                 v.ld, r, CW, W, RP, Ai, Ac, parts);
     else
-        k_residual_sq<__nv_bfloat16><<<G, kStreamRedThreads, 0, st>>>(
-            static_cast<const __nv_bfloat16*>(v.data), v.Ii, v.n_o, v.C, v.ld, r, W, RP, Ai, Ac, parts);
+        k_residual_sq<__nv_bfloat16><<<G, kStreamRedThreads, smem, st>>>(
+            static_cast<const __nv_bfloat16*>(v.data), v.Ii, v.n_o, v.C, v.ld, r, CW, W, RP, Ai, Ac, parts);
     count_launch();
     k_sum_parts<<<1, 256, 0, st>>>(parts, G, out);
     count_launch();
@@ -574,21 +674,35 @@ cudaError_t launch_residual_sq(const TensorView& v, int r, const float* W, int R
 }
 
 // ---------------------------------------------------------------------------
-// a8: bf16 cast with row pitch
+// a8: bf16 cast with row pitch; one thread per 8 destination elements
 // ---------------------------------------------------------------------------
 __global__ void k_to_bf16(const float* __restrict__ src, int64_t rows, int64_t C, int64_t ld_src,
                           __nv_bfloat16* __restrict__ dst, int64_t ld_dst) {
-    const int64_t n = rows * ld_dst;
+    const int64_t per_row = ld_dst / 8;
+    const int64_t n = rows * per_row;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = idx / ld_dst, c = idx % ld_dst;
-        dst[idx] = c < C ? __float2bfloat16_rn(src[row * ld_src + c]) : __float2bfloat16_rn(0.f);
+        const int64_t row = idx / per_row, c0 = (idx - row * per_row) * 8;
+        const float* sp = src + row * ld_src + c0;
+        float x[8];
+        // the source row holds C values in a pitch that is a multiple of 4
+        float4 a = c0 < C ? __ldg(reinterpret_cast<const float4*>(sp)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 b = c0 + 4 < C ? __ldg(reinterpret_cast<const float4*>(sp + 4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w, x[4] = b.x, x[5] = b.y, x[6] = b.z, x[7] = b.w;
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat16 lo = __float2bfloat16_rn(c0 + 2 * k < C ? x[2 * k] : 0.f);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(c0 + 2 * k + 1 < C ? x[2 * k + 1] : 0.f);
+            w[k] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+        *reinterpret_cast<uint4*>(dst + row * ld_dst + c0) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
 cudaError_t launch_to_bf16(const float* src, int64_t rows, int64_t C, int64_t ld_src, void* dst, int64_t ld_dst,
                            cudaStream_t st) {
-    int64_t g = (rows * ld_dst + 255) / 256;
+    int64_t g = (rows * (ld_dst / 8) + 255) / 256;
     if (g > 8 * num_sms()) g = 8 * num_sms();
     if (g < 1) g = 1;
     k_to_bf16<<<(int)g, 256, 0, st>>>(src, rows, C, ld_src, static_cast<__nv_bfloat16*>(dst), ld_dst);

@@ -24,7 +24,7 @@ struct Solver {
     float* X[NTF_MAX_ORDER][2] = {{nullptr}};
     double* GB[NTF_MAX_ORDER][2] = {{nullptr}};
     int* cur = nullptr;         // device [NTF_MAX_ORDER]
-    int* iters_dev = nullptr;   // device: completed outer iterations
+    int* iters_dev = nullptr;   // device: [0] completed outer iterations, [1] end-of-iteration ticket
     float* A[NTF_MAX_ORDER] = {nullptr};
     float* Ah[NTF_MAX_ORDER] = {nullptr};
     double* G[NTF_MAX_ORDER] = {nullptr};   // Grams of A
@@ -32,6 +32,7 @@ struct Solver {
     float* Aprev = nullptr;
     float* M = nullptr;
     double* V = nullptr;
+    float* Vf = nullptr;        // V in FP32 for the fused epilogue
     double* scal = nullptr;  // [0] ||T_s||^2 [1] F-hat [2] f_true [3] F-hat_0 [4] ||T_u||^2
     ntf_her_state* her = nullptr;
     void* ws_mt = nullptr;
@@ -122,8 +123,8 @@ struct Solver {
         return B;
     }
 
-    // one outer iteration on the fused path: per mode prep -> stream -> epilogue,
-    // then one small kernel for F_hat, the decision and the buffer flip
+    // one outer iteration on the fused path: per mode prep -> stream -> epilogue;
+    // the last epilogue also takes F_hat, the decision and the buffer flip
     ntf_status iterate_fused(cudaStream_t st) {
         const bool use_her = o.her != 0;
         unsigned char* ws = static_cast<unsigned char*>(ws_mt);
@@ -143,6 +144,7 @@ struct Solver {
             pp.Fc_rows_out = round_up(vs.C, 64);
             for (int l = 0; l < N; ++l) pp.dims[l] = vs.dims[l];
             pp.V = V;
+            pp.Vf = Vf;
             pp.Fc = (P.kind != ModeKind::Last && !P.tc) ? reinterpret_cast<float*>(ws + P.off_Fc) : nullptr;
             pp.FcT = P.tc ? reinterpret_cast<__nv_bfloat16*>(ws + P.off_Fc) : nullptr;
             pp.RPH = P.RPH;
@@ -172,29 +174,24 @@ struct Solver {
             ep.red = make_reduce_params(vs, P, reinterpret_cast<const float*>(ws + P.off_part),
                                         reinterpret_cast<const float*>(ws + P.off_W));
             ep.mode = n;
+            ep.order = N;
             ep.rows = vs.dims[n];
             ep.r = r;
             ep.last = n == N - 1 ? 1 : 0;
             ep.beta = &her->beta;
             ep.V = V;
+            ep.Vf = Vf;
             ep.gpart = gpart;
             ep.ipart = ipart;
             ep.qpart = qpart;
+            ep.ticket = iters_dev + 1;
+            ep.tnorm = &scal[0];
+            ep.fhat_out = &scal[1];
+            ep.iters_out = iters_dev;
+            ep.her = use_her ? her : nullptr;
             e = launch_epilogue(ep, st);
             if (e != cudaSuccess) return cuda_fail(e, "epilogue");
         }
-        FinishParams fp{};
-        fp.B = fb;
-        fp.order = N;
-        fp.blocks = epilogue_blocks(vs.dims[N - 1]);
-        fp.ipart = ipart;
-        fp.qpart = qpart;
-        fp.tnorm = &scal[0];
-        fp.fhat_out = &scal[1];
-        fp.iters_out = iters_dev;
-        fp.her = use_her ? her : nullptr;
-        cudaError_t e = launch_finish(fp, st);
-        if (e != cudaSuccess) return cuda_fail(e, "finish");
         return NTF_OK;
     }
 
@@ -233,7 +230,7 @@ struct Solver {
             e = launch_gram(Ah[n], rows, r, Gh[n], st);
             if (e != cudaSuccess) return cuda_fail(e, "gram");
         }
-        // F-hat_k = ||T||^2 - 2 <M_{N-1}, A_{N-1}> + sum(V_{N-1} (*) G(A_{N-1}))   (Alg. 2, line 9)
+        // F-hat_k = ||T||^2 - 2 <M_{N-1}, A_{N-1}> + sum(V_{N-1} (*) G(A_{N-1}))   (Alg. 2, restart test)
         const int last = N - 1;
         cudaError_t e = launch_objective(&scal[0], M, A[last], vs.dims[last], r, V, &scal[1], nullptr, st);
         if (e != cudaSuccess) return cuda_fail(e, "objective");
@@ -359,6 +356,7 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     if ((s = S->alloc((void**)&S->Aprev, sizeof(float) * maxrows * r)) != NTF_OK) return bail(s);
     if ((s = S->alloc((void**)&S->M, sizeof(float) * maxrows * r)) != NTF_OK) return bail(s);
     if ((s = S->alloc((void**)&S->V, sizeof(double) * r * r)) != NTF_OK) return bail(s);
+    if ((s = S->alloc((void**)&S->Vf, sizeof(float) * r * r)) != NTF_OK) return bail(s);
     if ((s = S->alloc((void**)&S->scal, sizeof(double) * 8)) != NTF_OK) return bail(s);
     if ((s = S->alloc((void**)&S->her, sizeof(ntf_her_state))) != NTF_OK) return bail(s);
     size_t ws = 0;
@@ -391,8 +389,12 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
                                                ~size_t(255)));
     cudaError_t e = launch_norm_sq(S->vs, parts, &S->scal[0], st);
     if (e != cudaSuccess) return bail(cuda_fail(e, "norm"));
-    e = launch_norm_sq(S->vu, parts, &S->scal[4], st);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "norm"));
+    if (S->vu.data != S->vs.data) {
+        e = launch_norm_sq(S->vu, parts, &S->scal[4], st);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "norm"));
+    } else {
+        NTF_CUDA_TRY(cudaMemcpyAsync(&S->scal[4], &S->scal[0], sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
     // Grams of A_0 (= A_hat_0)
     for (int l = 0; l < N; ++l) {
         e = launch_gram(S->X[l][0], S->vu.dims[l], r, S->GB[l][0], st);
@@ -623,8 +625,12 @@ ntf_status ntf_solve_host(const ntf_tensor* T_host, float* const* factors_host, 
         cudaGetLastError();
         return fail(NTF_ENOMEM, "cudaMalloc for the tensor failed");
     }
-    e = cudaMemcpy2DAsync(dT, ldd * es, T_host->data, ld * es, T_host->dims[T_host->order - 1] * es, rows,
-                          cudaMemcpyHostToDevice, st);
+    // one linear copy when the host rows already have the device pitch (no padding), else a pitched copy
+    if (ld == ldd)
+        e = cudaMemcpyAsync(dT, T_host->data, (size_t)rows * ldd * es, cudaMemcpyHostToDevice, st);
+    else
+        e = cudaMemcpy2DAsync(dT, ldd * es, T_host->data, ld * es, T_host->dims[T_host->order - 1] * es, rows,
+                              cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) {
         cudaFree(dT);
         return cuda_fail(e, "tensor upload");

@@ -27,6 +27,9 @@ SHAPES = [
     ((9, 300, 33), 64),       # maximum rank
     ((1, 1, 1), 3),           # degenerate
     ((2, 1, 130), 2),
+    ((150, 1000, 50), 12),    # the paper's unbalanced synthetic shape (Sec. 4.1)
+    ((150, 1000, 50), 25),
+    ((50, 50, 50), 10),       # the paper's cube
     ((1, 200, 1), 4),
 ]
 

@@ -176,3 +176,62 @@ def test_prepared_graph_with_timing_matches_eager():
     assert all(torch.equal(a, b) for a, b in zip(F1, F2))
     s1.close()
     s2.close()
+
+
+def test_solver_trajectory_unbalanced_shape():
+    # the paper's unbalanced synthetic shape 150 x 1000 x 50 (Sec. 4.1), rank 12
+    import paper_2001_04321_gb300 as ntf
+    dims, r, iters = (150, 1000, 50), 12, 6
+    T, init, buf, d, ld, Fd = _setup(dims, r, 1e-2, 1240)
+    fh, rs, rep = _trajectory(buf, d, ld, Fd, iters, ntf.Opts(max_iters=iters))
+    _, tr = oracle.solve(T, init, iters, her=True)
+    same = np.cumprod(rs == tr.restart).astype(bool)
+    k = int(same.sum())
+    assert k >= 3
+    np.testing.assert_allclose(fh[:k], tr.fhat[:k], rtol=0, atol=1e-6 * oracle.norm_sq(T))
+
+
+def test_solver_illconditioned_100cube_her_beats_plain():
+    # 100^3, rank 10, shared-base columns (ill-conditioned Grams), 0.1% noise:
+    # trajectory parity for the first iterations, then HER ahead of plain HALS
+    # after the same number of iterations (the paper's central claim, Sec. 4.2)
+    import paper_2001_04321_gb300 as ntf
+    w = synth.WORKLOADS["cube100_r10_illcond"]
+    dims, r = w["dims"], w["rank"]
+    T, init, buf, d, ld, Fd = _setup(dims, r, w["noise_rel"], w["seed"], recipe=w["recipe"])
+    fh, rs, _ = _trajectory(buf, d, ld, [A.clone() for A in Fd], 15, ntf.Opts(max_iters=15))
+    _, tr = oracle.solve(T, init, 15, her=True)
+    same = np.cumprod(rs == tr.restart).astype(bool)
+    k = int(same.sum())
+    assert k >= 5
+    np.testing.assert_allclose(fh[:k], tr.fhat[:k], rtol=0, atol=1e-6 * oracle.norm_sq(T))
+    F_her = [A.clone() for A in Fd]
+    rep_her = ntf.solve(buf, F_her, ntf.Opts(max_iters=300), dims=d, ld=ld)
+    F_plain = [A.clone() for A in Fd]
+    rep_plain = ntf.solve(buf, F_plain, ntf.Opts(her=False, max_iters=300), dims=d, ld=ld)
+    assert rep_her.f_true_last < rep_plain.f_true_last
+    assert rep_her.restarts > 0
+
+
+def test_solver_pgd_her_300cube_r32():
+    # 300^3, rank 32, PGD + HER: one iteration against the oracle at full size,
+    # then 200 iterations whose result is feasible, consistent and lower
+    import torch
+    import paper_2001_04321_gb300 as ntf
+    w = synth.WORKLOADS["cube300_r32"]
+    dims, r = w["dims"], w["rank"]
+    T, _ = synth.make_tensor(dims, r, w["noise_rel"], seed=w["seed"], recipe=w["recipe"])
+    init = synth.make_init(dims, r, seed=0)
+    Td = torch.from_numpy(T).cuda()
+    opts = ntf.Opts(method="pgd", inner_max=1, her=True, max_iters=1)
+    F = [torch.from_numpy(A).cuda() for A in init]
+    rep1 = ntf.solve(Td, F, opts)
+    Fo, tr = oracle.solve(T, init, 1, her=True, method="pgd", inner_max=1)
+    assert rep1.f_hat_last == pytest.approx(tr.fhat[0], rel=1e-5)
+    for a, b in zip(F, Fo):
+        assert rel_fro(a.cpu().numpy(), b) <= 1e-4
+    F = [torch.from_numpy(A).cuda() for A in init]
+    rep = ntf.solve(Td, F, ntf.Opts(method="pgd", inner_max=1, her=True, max_iters=200))
+    assert np.isfinite(rep.f_true_last) and rep.f_true_last < rep1.f_true_last
+    assert all(bool((A >= 0).all()) for A in F)
+    assert rep.f_true_last == pytest.approx(ntf.residual_sq(Td, F).item(), rel=1e-6)
