@@ -332,9 +332,14 @@ NTF_API ntf_status ntf_solver_prepare_graph(ntf_solver* s, int iters, void* stre
 NTF_API ntf_status ntf_solver_get_factors(ntf_solver* s, float* const* factors, void* stream);
 /* Synchronise and fill `report` (f_true_last computed explicitly here). */
 NTF_API ntf_status ntf_solver_report(ntf_solver* s, ntf_report* report, void* stream);
-/* Enable (1) / disable (0) CUDA-event timing of every MTTKRP streaming kernel
- * the solver launches; ntf_solver_mttkrp_time reads the totals (synchronises). */
-NTF_API ntf_status ntf_solver_set_timing(ntf_solver* s, int on);
+/* CUDA-event timing of the MTTKRP streaming kernels: every `every`-th outer
+ * iteration (counted from the start of each captured graph, or across eager
+ * runs) records an event pair around each of its streaming launches; 1 times
+ * every iteration, 0 turns timing off.  ntf_solver_mttkrp_time reads the
+ * totals (synchronises).  A timed launch and the kernel after it are launched
+ * without programmatic dependent launch, so their times carry no overlap with
+ * the neighbouring kernels. */
+NTF_API ntf_status ntf_solver_set_timing(ntf_solver* s, int every);
 NTF_API ntf_status ntf_solver_mttkrp_time(ntf_solver* s, double* total_ms, int64_t* launches, double* bytes_per_launch,
                                   void* stream);
 NTF_API void ntf_solver_destroy(ntf_solver* s);

@@ -466,8 +466,9 @@ class Solver:
         _check(load().ntf_solver_report(self._h, C.byref(rep), _stream(stream)))
         return _report(rep)
 
-    def set_timing(self, on: bool):
-        _check(load().ntf_solver_set_timing(self._h, int(on)))
+    def set_timing(self, every):
+        """Time the MTTKRP streams of every ``every``-th iteration (True = 1, False/0 = off)."""
+        _check(load().ntf_solver_set_timing(self._h, int(every)))
 
     def mttkrp_time(self, stream=None):
         ms = C.c_double()

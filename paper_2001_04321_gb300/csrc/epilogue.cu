@@ -29,9 +29,12 @@
 
 namespace ntf {
 
+// Epilogue CTA: 4 rows of mode n, 8 warps.  Output M(j, p) of row j is the sum of
+// two pieces of the stream's partials, taken by warp j and warp j + 4 (lane p);
+// the HALS sweep of row j then runs on warp j alone.
 constexpr int kEpiWarps = 8;
-constexpr int kEpiRowsPerWarp = 2;
-constexpr int kEpiRows = kEpiWarps * kEpiRowsPerWarp;   // rows per CTA
+constexpr int kEpiRows = 4;                              // rows per CTA
+constexpr int kEpiPieces = kEpiWarps / kEpiRows;         // partial-sum pieces per output
 
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
@@ -52,69 +55,79 @@ __device__ __forceinline__ float warp_allsum_f(float v) {
     return v;
 }
 
-// Gram entry q (k = 0: A, 1: A_hat) from the epilogue CTAs' partials: lane u adds
-// the partials of CTAs u, u + 32, ... in order, then a butterfly over the lanes.
-// Every entry of a Gram of nonnegative factors is a sum of nonnegative terms,
-// so FP32 summation keeps a relative error of a few units in the last place.
-__device__ __forceinline__ float gram_entry(const float* gpart, int nblk, int rr, int k, int q, int lane) {
-    const float* base = gpart + (int64_t)k * rr + q;
-    const int64_t stride = 2 * (int64_t)rr;
-    float s = 0.f;
-    for (int b = lane; b < nblk; b += 32) s += base[(int64_t)b * stride];
-    return warp_allsum_f(s);
-}
-
 // pairing factor A_hat_l as seen by the update of mode n (eq. NNLS_her_exact):
-// modes already updated in this iteration use their extrapolated buffer
-__device__ __forceinline__ const float* pairing_factor(const FusedBufs& B, int l, int n) {
-    const int c = B.cur[l];
+// modes already updated in this iteration use their extrapolated buffer;
+// cbuf holds the current buffer index of every mode
+__device__ __forceinline__ const float* pairing_factor_c(const FusedBufs& B, int l, int n, const int* cbuf) {
+    const int c = cbuf[l];
     return (B.her && l < n) ? B.X[l][1 - c] : B.X[l][c];
-}
-__device__ __forceinline__ const double* pairing_gram(const FusedBufs& B, int l, int n) {
-    const int c = B.cur[l];
-    return (B.her && l < n) ? B.GB[l][1 - c] : B.GB[l][c];
 }
 
 // ---------------------------------------------------------------------------
 // prep
 // ---------------------------------------------------------------------------
 __global__ void k_prep(const PrepParams P) {
+    pdl_wait();
+    pdl_trigger();
     const int rr = P.r * P.r;
     const int n = P.mode;
     const FusedBufs& B = P.B;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // Control words first, all loads in flight together: the current buffer of
+    // every mode (lane l holds mode l's), the iteration count and the last decision.
+    const int cur_l = lane < P.order ? B.cur[lane] : 0;
+    const int iters = *B.iters;
+    const int last_restart = P.her ? P.her->last_restart : 1;
+    int cbuf[NTF_MAX_ORDER];
+#pragma unroll
+    for (int l = 0; l < NTF_MAX_ORDER; ++l) cbuf[l] = __shfl_sync(0xffffffffu, cur_l, l);
     // Gram finishing for fin_mode; at mode 0 only once an iteration has completed
     const bool end_of_iter = n == 0;
-    const bool fin = P.fin_mode >= 0 && (!end_of_iter || *B.iters > 0);
+    const bool fin = P.fin_mode >= 0 && (!end_of_iter || iters > 0);
     const bool two = fin && !end_of_iter && B.her;     // mid-iteration with HER: Grams of A and A_hat
-    const int nVG = rr * (two ? 2 : 1);
+    // at the end of an iteration the kept Gram of the last mode: A_hat's after an accept, else A's
+    const bool keep_hat = end_of_iter && B.her && last_restart == 0;
+
     // (1) the finished Grams of fin_mode and V_n: one warp per entry q, the
-    // warps of different blocks first
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warps of different blocks first.  The partials of both Grams and both
+    // buffers of every other mode's Gram are loaded before anything is chosen.
     const int nwarps = gridDim.x * (blockDim.x >> 5);
-    const int keep = (end_of_iter && B.her && P.her && P.her->last_restart == 0) ? 1 : 0;
     for (int q = blockIdx.x + gridDim.x * warp; q < rr; q += nwarps) {
-        float sA = 0.f, sH = 0.f;
-        if (fin) {
-            sA = gram_entry(P.gpart, P.fin_blocks, rr, end_of_iter ? keep : 0, q, lane);
-            if (two) sH = gram_entry(P.gpart, P.fin_blocks, rr, 1, q, lane);
+        float pa = 0.f, ph = 0.f;
+        const float* base = P.gpart + q;
+        for (int b = lane; b < P.fin_blocks; b += 32) {
+            pa += base[(int64_t)(2 * b) * rr];
+            if (B.her) ph += base[(int64_t)(2 * b + 1) * rr];
+        }
+        // lane 2l + k: entry q of the Gram held in buffer k of mode l
+        const int gl_mode = lane >> 1, gl_buf = lane & 1;
+        const double gq = (gl_mode < P.order && gl_mode != n) ? B.GB[gl_mode][gl_buf][q] : 0.0;
+        pa = warp_allsum_f(pa);
+        ph = warp_allsum_f(ph);
+        double gsel[NTF_MAX_ORDER];
+#pragma unroll
+        for (int l = 0; l < NTF_MAX_ORDER; ++l) {
+            // the pairing buffer of mode l (eq. NNLS_her_exact): A_hat for modes already updated
+            const int k = (B.her && l < n) ? 1 - cbuf[l] : cbuf[l];
+            const double g0 = __shfl_sync(0xffffffffu, gq, 2 * l);
+            const double g1 = __shfl_sync(0xffffffffu, gq, 2 * l + 1);
+            gsel[l] = k ? g1 : g0;
         }
         if (lane == 0) {
             double v = 1.0;
-            for (int l = 0; l < P.order; ++l) {
-                if (l == n) continue;
-                double gl;
+#pragma unroll
+            for (int l = 0; l < NTF_MAX_ORDER; ++l) {
+                if (l >= P.order || l == n) continue;
+                double gl = gsel[l];
                 if (fin && l == P.fin_mode) {
-                    const int c = B.cur[l];
-                    // end of iteration: the kept factor (A on restart, A_hat on accept), already current;
-                    // mid-iteration with HER: A_{n-1} is stored, A_hat_{n-1} pairs with mode n
-                    B.GB[l][c][q] = (double)sA;
-                    gl = (double)sA;
+                    const int c = cbuf[l];
+                    const double gA = (double)((end_of_iter && keep_hat) ? ph : pa);
+                    B.GB[l][c][q] = gA;   // the kept factor (end of iteration) or A_{n-1}
+                    gl = gA;
                     if (two) {
-                        gl = (double)sH;
+                        gl = (double)ph;   // A_hat_{n-1} pairs with mode n
                         B.GB[l][1 - c][q] = gl;
                     }
-                } else {
-                    gl = pairing_gram(B, l, n)[q];
                 }
                 v *= gl;
             }
@@ -123,6 +136,9 @@ __global__ void k_prep(const PrepParams P) {
         }
     }
     // (2) packed factors and weights
+    const float* src_fc = P.Fc ? pairing_factor_c(B, P.order - 1, n, cbuf)
+                               : P.FcT ? pairing_factor_c(B, P.fct_mode, n, cbuf) : nullptr;
+    const float* src_fi = P.Fi ? pairing_factor_c(B, P.order - 2, n, cbuf) : nullptr;
     const int64_t nFc = P.Fc ? P.Fc_rows_out * P.RP : P.FcT ? (int64_t)P.n_kc * 2 * P.RPH * 64 : 0;
     const int64_t nFi = P.Fi ? P.Ii * P.RP : 0;
     const int64_t nW = P.W ? P.n_o * P.RP : 0;
@@ -132,13 +148,13 @@ __global__ void k_prep(const PrepParams P) {
         int64_t k = idx;
         if (k < nFc) {
             if (P.Fc) {
-                const float* src = pairing_factor(B, P.order - 1, n);
+                const float* src = src_fc;
                 const int64_t i = k / P.RP;
                 const int p = (int)(k % P.RP);
                 P.Fc[k] = (i < P.C && p < P.r) ? src[i * P.r + p] : 0.f;
             } else {
                 // tensor-core B operand: bf16 hi | lo columns, 128-byte rows, swizzled like a TMA box
-                const float* src = pairing_factor(B, P.fct_mode, n);
+                const float* src = src_fc;
                 const int N = 2 * P.RPH;
                 const int kl = (int)(k % 64);
                 const int nn = (int)((k / 64) % N);
@@ -154,7 +170,7 @@ __global__ void k_prep(const PrepParams P) {
         }
         k -= nFc;
         if (k < nFi) {
-            const float* src = pairing_factor(B, P.order - 2, n);
+            const float* src = src_fi;
             const int64_t i = k / P.RP;
             const int p = (int)(k % P.RP);
             P.Fi[k] = p < P.r ? src[i * P.r + p] : 0.f;
@@ -168,10 +184,12 @@ __global__ void k_prep(const PrepParams P) {
             if (p < P.r) {
                 w = 1.f;
                 int64_t rem = o;
-                for (int l = P.order - 3; l >= 0; --l) {
+#pragma unroll
+                for (int l = NTF_MAX_ORDER - 3; l >= 0; --l) {
+                    if (l > P.order - 3) continue;
                     const int64_t il = rem % P.dims[l];
                     rem /= P.dims[l];
-                    if (l != P.skip) w *= pairing_factor(B, l, n)[il * P.r + p];
+                    if (l != P.skip) w *= pairing_factor_c(B, l, n, cbuf)[il * P.r + p];
                 }
             }
             P.W[k] = w;
@@ -179,26 +197,29 @@ __global__ void k_prep(const PrepParams P) {
     }
 }
 
-cudaError_t launch_prep(const PrepParams& P, cudaStream_t st) {
+cudaError_t launch_prep(const PrepParams& P, cudaStream_t st, bool pdl) {
     const int64_t total = (int64_t)32 * P.r * P.r +
                           (P.Fc ? P.Fc_rows_out * P.RP : P.FcT ? (int64_t)P.n_kc * 2 * P.RPH * 64 : 0) +
                           (P.Fi ? P.Ii * P.RP : 0) + (P.W ? P.n_o * P.RP : 0);
     int64_t g = (total + 255) / 256;
     if (g > 2 * num_sms()) g = 2 * num_sms();
     if (g < 8) g = 8;
-    k_prep<<<(int)g, 256, 0, st>>>(P);
+    cudaError_t e = launch_kernel(k_prep, dim3((unsigned)g), dim3(256), 0, st, pdl, P);
     count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 // ---------------------------------------------------------------------------
 // epilogue
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float Vs[32 * 33];
     __shared__ float rinv[32];
     __shared__ float rowsA[kEpiRows][32];
     __shared__ float rowsH[kEpiRows][32];
+    __shared__ float mpiece[kEpiPieces - 1][kEpiRows][32];
     __shared__ float winner[kEpiWarps];
     __shared__ double dred[kEpiWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -213,66 +234,52 @@ __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) 
     }
     const float beta = her ? (float)*P.beta : 0.f;
 
-    // M rows from the stream's partial sums, and the previous rows
-    int64_t row[kEpiRowsPerWarp];
-    float m[kEpiRowsPerWarp], a[kEpiRowsPerWarp], a_old[kEpiRowsPerWarp];
-#pragma unroll
-    for (int k = 0; k < kEpiRowsPerWarp; ++k) {
-        row[k] = (int64_t)blockIdx.x * kEpiRows + warp * kEpiRowsPerWarp + k;
-        const bool live = row[k] < P.rows && lane < r;
-        a_old[k] = live ? A[row[k] * r + lane] : 0.f;
-        m[k] = live ? reduce_output(P.red, row[k], lane) : 0.f;
-        a[k] = a_old[k];
-    }
+    // M row pieces from the stream's partial sums, and the previous row
+    const int rw = warp % kEpiRows, piece = warp / kEpiRows;
+    const int64_t row = (int64_t)blockIdx.x * kEpiRows + rw;
+    const bool live = row < P.rows && lane < r;
+    const float a_old = (live && piece == 0) ? A[row * r + lane] : 0.f;
+    float m = live ? reduce_piece(P.red, row, lane, piece, kEpiPieces) : 0.f;
+    if (piece > 0) mpiece[piece - 1][rw][lane] = m;
     __syncthreads();
     if (threadIdx.x < 32) {
         const float d = Vs[threadIdx.x * 33 + threadIdx.x];
         rinv[threadIdx.x] = (threadIdx.x < r && d > 0.f) ? 1.f / d : 0.f;
     }
-    __syncthreads();
-
-    // residual g_p = M_p - sum_l a_l V(l,p), lane p
-    float g[kEpiRowsPerWarp];
+    float a = a_old, ah = 0.f, inner = 0.f;
+    if (piece == 0) {
 #pragma unroll
-    for (int k = 0; k < kEpiRowsPerWarp; ++k) g[k] = m[k];
-    for (int l = 0; l < r; ++l) {
-        const float vlp = Vs[l * 33 + lane];
-#pragma unroll
-        for (int k = 0; k < kEpiRowsPerWarp; ++k) g[k] = fmaf(-__shfl_sync(0xffffffffu, a[k], l), vlp, g[k]);
+        for (int k = 0; k < kEpiPieces - 1; ++k) m += mpiece[k][rw][lane];
     }
-    // one HALS sweep: a_j <- max(0, M_j - sum_{l != j} a_l V_lj) / V_jj = max(0, g_j + a_j V_jj) / V_jj
-    for (int jj = 0; jj < r; ++jj) {
-        const float vjj = Vs[jj * 33 + jj];
-        const float rj = rinv[jj];
-        const float vjp = Vs[jj * 33 + lane];
-#pragma unroll
-        for (int k = 0; k < kEpiRowsPerWarp; ++k) {
+    __syncthreads();
+    if (piece == 0) {
+        // residual g_p = M_p - sum_l a_l V(l,p), lane p
+        float g = m;
+        for (int l = 0; l < r; ++l) g = fmaf(-__shfl_sync(0xffffffffu, a, l), Vs[l * 33 + lane], g);
+        // one HALS sweep: a_j <- max(0, M_j - sum_{l != j} a_l V_lj) / V_jj = max(0, g_j + a_j V_jj) / V_jj
+        for (int jj = 0; jj < r; ++jj) {
+            const float vjj = Vs[jj * 33 + jj];
+            const float rj = rinv[jj];
             float delta = 0.f;
             if (lane == jj && rj > 0.f) {
-                const float nv = fmaxf(fmaf(a[k], vjj, g[k]), 0.f) * rj;
-                delta = nv - a[k];
-                a[k] = nv;
+                const float nv = fmaxf(fmaf(a, vjj, g), 0.f) * rj;
+                delta = nv - a;
+                a = nv;
             }
             delta = __shfl_sync(0xffffffffu, delta, jj);
-            g[k] = fmaf(-delta, vjp, g[k]);
+            g = fmaf(-delta, Vs[jj * 33 + lane], g);
         }
-    }
-
-    float inner = 0.f;
-#pragma unroll
-    for (int k = 0; k < kEpiRowsPerWarp; ++k) {
-        const bool live = row[k] < P.rows && lane < r;
-        float ah = a[k];
+        ah = a;
         if (live) {
-            A[row[k] * r + lane] = a[k];
+            A[row * r + lane] = a;
             if (her) {
-                ah = fmaxf(fmaf(beta, a[k] - a_old[k], a[k]), 0.f);
-                Ah[row[k] * r + lane] = ah;
+                ah = fmaxf(fmaf(beta, a - a_old, a), 0.f);
+                Ah[row * r + lane] = ah;
             }
-            inner = fmaf(m[k], a[k], inner);
+            inner = m * a;
         }
-        rowsA[warp * kEpiRowsPerWarp + k][lane] = live ? a[k] : 0.f;
-        rowsH[warp * kEpiRowsPerWarp + k][lane] = live ? ah : 0.f;
+        rowsA[rw][lane] = live ? a : 0.f;
+        rowsH[rw][lane] = live ? ah : 0.f;
     }
     inner = warp_sum_f(inner);
     if (lane == 0) winner[warp] = inner;
@@ -323,46 +330,61 @@ __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) 
     __syncthreads();
     if (!is_last || warp != 0) return;
     __threadfence();
+    // everything the decision reads is loaded before anything is stored, so the
+    // loads are in flight together
     double isum = 0.0, qsum = 0.0;
     for (int b = lane; b < (int)gridDim.x; b += 32) {
         isum += __ldcg(P.ipart + b);
         qsum += __ldcg(P.qpart + b);
     }
+    const double tn = __ldcg(P.tnorm);
+    const int it = __ldcg(P.iters_out);
+    const int cl = lane < P.order ? __ldcg(P.B.cur + lane) : 0;
+    ntf_her_state hs{};
+    if (P.her) {
+        hs.beta = __ldcg(&P.her->beta);
+        hs.beta_bar = __ldcg(&P.her->beta_bar);
+        hs.f_hat_prev = __ldcg(&P.her->f_hat_prev);
+        hs.gamma = __ldcg(&P.her->gamma);
+        hs.gamma_bar = __ldcg(&P.her->gamma_bar);
+        hs.eta = __ldcg(&P.her->eta);
+        hs.iters = __ldcg(&P.her->iters);
+        hs.restarts = __ldcg(&P.her->restarts);
+    }
     isum = warp_sum_dd(isum);
     qsum = warp_sum_dd(qsum);
+    const double fhat = tn - 2.0 * isum + qsum;
+    // Alg. 2: restart if F_hat_k > F_hat_{k-1}; a non-finite F_hat restarts and is flagged
+    const bool finite = isfinite(fhat);
+    const int restart = (!finite || fhat > hs.f_hat_prev) ? 1 : 0;
+    if (P.her && !restart && lane < P.order) P.B.cur[lane] = 1 - cl;   // keep A_hat_k: A_k <- A_hat_k
     if (lane != 0) return;
     *P.ticket = 0;
-    const double fhat = *P.tnorm - 2.0 * isum + qsum;
     *P.fhat_out = fhat;
-    *P.iters_out += 1;
+    *P.iters_out = it + 1;
     if (!P.her) return;
-    // Alg. 2: restart if F_hat_k > F_hat_{k-1}; a non-finite F_hat restarts and is flagged
-    ntf_her_state* hs = P.her;
-    const double b0 = hs->beta, bb = hs->beta_bar;
-    const bool finite = isfinite(fhat);
-    const int restart = (!finite || fhat > hs->f_hat_prev) ? 1 : 0;
+    ntf_her_state* out = P.her;
     if (restart) {
-        hs->beta_bar = b0;
-        hs->beta = b0 / hs->eta;
+        out->beta_bar = hs.beta;
+        out->beta = hs.beta / hs.eta;
     } else {
-        hs->beta_bar = fmin(1.0, hs->gamma_bar * bb);
-        hs->beta = fmin(bb, hs->gamma * b0);
-        // keep the extrapolated sequence: A_k <- A_hat_k for every block
-        for (int l = 0; l < P.order; ++l) P.B.cur[l] = 1 - P.B.cur[l];
+        out->beta_bar = fmin(1.0, hs.gamma_bar * hs.beta_bar);
+        out->beta = fmin(hs.beta_bar, hs.gamma * hs.beta);
     }
-    hs->f_hat_prev = fhat;
-    hs->iters += 1;
-    hs->restarts += restart;
-    hs->last_restart = restart;
-    if (!finite) hs->numeric_error = 1;
+    out->f_hat_prev = fhat;
+    out->iters = hs.iters + 1;
+    out->restarts = hs.restarts + restart;
+    out->last_restart = restart;
+    if (!finite) out->numeric_error = 1;
 }
 
 int epilogue_blocks(int64_t rows) { return (int)((rows + kEpiRows - 1) / kEpiRows); }
 
-cudaError_t launch_epilogue(const EpiParams& P, cudaStream_t st) {
-    k_epilogue<<<epilogue_blocks(P.rows), kEpiWarps * 32, 0, st>>>(P);
+cudaError_t launch_epilogue(const EpiParams& P, cudaStream_t st, bool pdl) {
+    cudaError_t e = launch_kernel(k_epilogue, dim3((unsigned)epilogue_blocks(P.rows)), dim3(kEpiWarps * 32), 0, st,
+                                  pdl, P);
     count_launch();
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace ntf

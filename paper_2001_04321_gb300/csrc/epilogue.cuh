@@ -62,12 +62,12 @@ struct EpiParams {
     ntf_her_state* her;    // nullptr without HER
 };
 
-cudaError_t launch_prep(const PrepParams& P, cudaStream_t st);
-cudaError_t launch_epilogue(const EpiParams& P, cudaStream_t st);
+cudaError_t launch_prep(const PrepParams& P, cudaStream_t st, bool pdl);
+cudaError_t launch_epilogue(const EpiParams& P, cudaStream_t st, bool pdl);
 int epilogue_blocks(int64_t rows);
 
 // streaming kernel of a plan alone (the packed factors / W already in place)
 ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* workspace, cudaStream_t st,
-                             TmapCache* cache, StreamTimer* timer);
+                             TmapCache* cache, StreamTimer* timer, bool pdl = false);
 
 }  // namespace ntf

@@ -3,7 +3,7 @@
 
 namespace ntf {
 cudaError_t launch_stream_f32(int kind, int R, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
-                              const StreamParams& P) {
-    return launch_stream_impl<float>(kind, R, grid, smem, st, map, P);
+                              const StreamParams& P, bool pdl) {
+    return launch_stream_impl<float>(kind, R, grid, smem, st, map, P, pdl);
 }
 }  // namespace ntf

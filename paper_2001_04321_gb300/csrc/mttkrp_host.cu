@@ -153,12 +153,16 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
         const int per_sm = (P.tc && 2 * tc_rows_smem(P.RPH) <= 227 * 1024) ? 2 : 1;
         P.G = (int)std::min<int64_t>(P.n_tiles, (int64_t)sms * per_sm);
     }
+    // tensor-core row kernels split the work at 64-column chunks (a tile then meets at most
+    // two CTAs, since G <= n_tiles); the others at whole tiles
+    P.upt = (P.tc && P.kind != ModeKind::Last) ? P.n_kc : 1;
     P.Smax = 1;
     if (P.kind == ModeKind::Inner) {
+        const int64_t U = P.n_tiles * P.upt;
         for (int g = 0; g < P.G; ++g) {
-            const int64_t b = (P.n_tiles * g) / P.G, e = (P.n_tiles * (g + 1)) / P.G;
+            const int64_t b = (U * g) / P.G, e = (U * (g + 1)) / P.G;
             if (e > b) {
-                const int s = (int)((e - 1) / P.n_ot - b / P.n_ot + 1);
+                const int s = (int)(((e - 1) / P.upt) / P.n_ot - (b / P.upt) / P.n_ot + 1);
                 if (s > P.Smax) P.Smax = s;
             }
         }
@@ -184,6 +188,9 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     else
         part = (size_t)P.G * P.Cpad * P.RP;
     off = align256(off + sizeof(float) * part);
+    // outer mode with split tiles: the part of a tile held by the CTA whose range ends inside it
+    P.off_tail = off;
+    if (P.kind == ModeKind::Outer && P.upt > 1) off = align256(off + sizeof(float) * (size_t)P.G * P.RP);
     P.total = off;
     *p = P;
     return NTF_OK;
@@ -286,7 +293,11 @@ ReduceParams make_reduce_params(const TensorView& v, const MttkrpPlan& P, const 
     R.RP = P.RP;
     R.r = P.rank;
     R.part_warps = P.tc ? 1 : kStreamWarps;
+    R.upt = P.upt;
     R.part = part;
+    R.tail = (P.kind == ModeKind::Outer && P.upt > 1)
+                 ? reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(part) + (P.off_tail - P.off_part))
+                 : nullptr;
     R.W = W;
     if (P.kind == ModeKind::Outer) {
         R.In = v.dims[P.mode];
@@ -335,7 +346,7 @@ static ntf_status get_tensor_map(const TensorView& v, const MttkrpPlan& P, TmapC
 }
 
 ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* workspace, cudaStream_t st,
-                             TmapCache* cache, StreamTimer* timer) {
+                             TmapCache* cache, StreamTimer* timer, bool pdl) {
     unsigned char* ws = static_cast<unsigned char*>(workspace);
     CUtensorMap local_map;
     const CUtensorMap* map = nullptr;
@@ -374,6 +385,8 @@ ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* wor
         T.n_ot = P.n_ot;
         T.n_tiles = P.n_tiles;
         T.n_kc = P.n_kc;
+        T.upt = P.upt;
+        T.tail = (P.kind == ModeKind::Outer && P.upt > 1) ? reinterpret_cast<float*>(ws + P.off_tail) : nullptr;
         T.RP = P.RP;
         T.r = P.rank;
         T.Smax = P.Smax;
@@ -386,7 +399,7 @@ ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* wor
         grid = P.kind == ModeKind::Last ? dim3(P.G, P.n_cb, 1) : dim3(P.G, 1, 1);
         smem = P.kind == ModeKind::Last ? tc_last_smem(P.RPH) : tc_rows_smem(P.RPH);
         if (timer && timer->start) NTF_CUDA_TRY(record_timer_event(timer->start, st));
-        e = launch_stream_tc(kind, P.RPH, grid, smem, st, *map, T);
+        e = launch_stream_tc(kind, P.RPH, grid, smem, st, *map, T, pdl && !timer);
     } else {
         if (P.kind == ModeKind::Last) {
             grid = dim3(P.G, P.n_cb, P.n_pb);
@@ -396,8 +409,8 @@ ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* wor
             smem = stream_rows_smem(v.es, P.RP);
         }
         if (timer && timer->start) NTF_CUDA_TRY(record_timer_event(timer->start, st));
-        e = v.dtype == NTF_F32 ? launch_stream_f32(kind, P.R, grid, smem, st, *map, S)
-                               : launch_stream_bf16(kind, P.R, grid, smem, st, *map, S);
+        e = v.dtype == NTF_F32 ? launch_stream_f32(kind, P.R, grid, smem, st, *map, S, pdl && !timer)
+                               : launch_stream_bf16(kind, P.R, grid, smem, st, *map, S, pdl && !timer);
     }
     count_launch();
     if (e != cudaSuccess) return cuda_fail(e, "MTTKRP streaming kernel launch");

@@ -138,6 +138,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_wait();
+    pdl_trigger();
 
     if (warp == kStreamWarps) {
         // ------------------------------ producer ------------------------------
@@ -402,6 +404,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_wait();
+    pdl_trigger();
 
     if (warp == kStreamWarps) {
         // ------------------------------ producer ------------------------------
@@ -539,9 +543,9 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
 
 // per-dtype launchers (mttkrp_f32.cu / mttkrp_bf16.cu)
 cudaError_t launch_stream_f32(int kind, int R, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
-                              const StreamParams& P);
+                              const StreamParams& P, bool pdl = false);
 cudaError_t launch_stream_bf16(int kind, int R, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
-                               const StreamParams& P);
+                               const StreamParams& P, bool pdl = false);
 
 }  // namespace ntf
 
@@ -551,7 +555,7 @@ namespace ntf {
 // kind: 0 = inner, 1 = outer, 2 = last.  R in {4, 8, 12, 16, 20, 24, 32}.
 template <typename TE>
 cudaError_t launch_stream_impl(int kind, int R, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
-                               const StreamParams& P) {
+                               const StreamParams& P, bool pdl) {
     typedef void (*Kern)(const CUtensorMap, const StreamParams);
     Kern k = nullptr;
 #define NTF_PICK(RR)                                                \
@@ -575,8 +579,7 @@ cudaError_t launch_stream_impl(int kind, int R, dim3 grid, size_t smem, cudaStre
         set_bytes[kind][ri] = smem;
     }
     if (grid.x == 0) return cudaSuccess;   // configuration only
-    k<<<grid, kStreamThreads, smem, st>>>(map, P);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, dim3(kStreamThreads), smem, st, pdl, map, P);
 }
 
 }  // namespace ntf

@@ -12,83 +12,120 @@ struct ReduceParams {
     int64_t n_tiles, n_ot, nb, Ii, n_o, C, Cpad;
     int G, Smax, I_T, RP, r;
     int part_warps;               // inner mode: partial slots per CTA (8 per-warp, or 1)
+    int upt;                      // work units per tile (CTAs own contiguous unit ranges)
     int64_t In, stride, hi_count;  // outer mode: o = (hi*In + j)*stride + lo
     const float* part;
     const float* W;
+    const float* tail;            // outer mode, split tiles: per-CTA part of the tile its range ends in
 };
 
 #ifdef __CUDACC__
+// Every reduction below is a fixed-order sum over an index range that can be
+// split into H contiguous pieces (piece h of H); the caller adds the pieces in
+// order h = 0..H-1, so the result does not depend on how the work was spread.
+// Loads go out 32 at a time, predicated, so that one piece costs one or two
+// round trips to L2.
+
 // Inner mode: partials per (CTA, segment, warp, row-in-block).  Only the CTAs
 // whose contiguous tile range meets inner block ib contribute.
-__device__ __forceinline__ float reduce_inner(const ReduceParams& P, int64_t j, int p) {
+__device__ __forceinline__ float reduce_inner(const ReduceParams& P, int64_t j, int p, int h, int H) {
     const int64_t ib = j / P.I_T;
     const int b = (int)(j % P.I_T);
-    const int64_t t0 = ib * P.n_ot, t1 = t0 + P.n_ot;   // tiles of block ib
-    // CTA g owns tiles [floor(n_tiles g / G), floor(n_tiles (g+1) / G)); the CTA owning tile t is
-    // floor(((t + 1) G - 1) / n_tiles)
-    const int g0 = (int)(((t0 + 1) * P.G - 1) / P.n_tiles);
-    const int g1 = (int)((t1 * P.G - 1) / P.n_tiles);
+    // units (upt per tile) of block ib: [u0, u1).  CTA g owns units [floor(U g / G),
+    // floor(U (g+1) / G)); the CTA owning unit u is floor(((u + 1) G - 1) / U)
+    const int64_t U = P.n_tiles * P.upt;
+    const int64_t u0 = ib * P.n_ot * P.upt, u1 = u0 + P.n_ot * P.upt;
+    const int g0 = (int)(((u0 + 1) * P.G - 1) / U);
+    const int g1 = (int)((u1 * P.G - 1) / U);
     // CTA g0 may have started in an earlier block (segment ib - its first block); every later
     // CTA that meets block ib starts inside it (segment 0)
-    const int seg0 = (int)(ib - ((P.n_tiles * g0) / P.G) / P.n_ot);
+    const int seg0 = (int)(ib - (((U * g0) / P.G) / P.upt) / P.n_ot);
+    const int cnt = g1 - g0 + 1;
+    const int ga = g0 + (cnt * h) / H, gb = g0 + (cnt * (h + 1)) / H;   // this piece: CTAs [ga, gb)
     const int64_t slot = (int64_t)P.part_warps * P.I_T * P.RP;          // one (CTA, segment) slot
+    const int64_t wstride = (int64_t)P.I_T * P.RP;
     const float* q = P.part + (int64_t)b * P.RP + p;
     float s = 0.f;
     if (P.part_warps == 1) {
-        // one partial per CTA: up to 16 independent loads in flight, summed in order
-        s = q[((int64_t)g0 * P.Smax + seg0) * slot];
-        for (int g = g0 + 1; g <= g1; g += 16) {
-            float x[16];
+        for (int g = ga; g < gb; g += 32) {
+            float x[32];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) x[u] = (g + u <= g1) ? q[((int64_t)(g + u) * P.Smax) * slot] : 0.f;
+            for (int u = 0; u < 32; ++u) {
+                const int gg = g + u;
+                x[u] = gg < gb ? q[((int64_t)gg * P.Smax + (gg == g0 ? seg0 : 0)) * slot] : 0.f;
+            }
 #pragma unroll
-            for (int u = 0; u < 16; ++u) s += x[u];
+            for (int u = 0; u < 32; ++u) s += x[u];
         }
         return s;
     }
-    for (int w = 0; w < P.part_warps; ++w) s += q[((int64_t)g0 * P.Smax + seg0) * slot + (int64_t)w * P.I_T * P.RP];
-    for (int g = g0 + 1; g <= g1; ++g) {
-        float x[8];
+    for (int g = ga; g < gb; g += 4) {
+        float x[4][8];
 #pragma unroll
-        for (int w = 0; w < 8; ++w) x[w] = w < P.part_warps ? q[((int64_t)g * P.Smax) * slot + (int64_t)w * P.I_T * P.RP] : 0.f;
+        for (int u = 0; u < 4; ++u) {
+            const int gg = g + u;
+            const float* qg = q + ((int64_t)gg * P.Smax + (gg == g0 ? seg0 : 0)) * slot;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) s += x[w];
+            for (int w = 0; w < 8; ++w) x[u][w] = (gg < gb && w < P.part_warps) ? qg[w * wstride] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s += x[u][w];
     }
     return s;
 }
 
 // Outer mode: one partial per tile (o, ib), weighted by W(o, p), summed over
-// all outer indices o with i_n(o) = j.
-__device__ __forceinline__ float reduce_outer(const ReduceParams& P, int64_t j, int p) {
+// all outer indices o with i_n(o) = j (piece h takes a contiguous range of them).
+__device__ __forceinline__ float reduce_outer(const ReduceParams& P, int64_t j, int p, int h, int H) {
+    const int64_t n = P.hi_count * P.stride;
+    const int64_t ka = (n * h) / H, kb = (n * (h + 1)) / H;
     float s = 0.f;
-    for (int64_t hi = 0; hi < P.hi_count; ++hi)
-        for (int64_t lo = 0; lo < P.stride; ++lo) {
-            const int64_t o = (hi * P.In + j) * P.stride + lo;
-            float so = 0.f;
+    for (int64_t k = ka; k < kb; ++k) {
+        const int64_t hi = k / P.stride, lo = k - hi * P.stride;
+        const int64_t o = (hi * P.In + j) * P.stride + lo;
+        float so = 0.f;
 #pragma unroll 4
-            for (int64_t ib = 0; ib < P.nb; ++ib) so += P.part[(o * P.nb + ib) * P.RP + p];
-            s = fmaf(P.W[o * P.RP + p], so, s);
+        for (int64_t ib = 0; ib < P.nb; ++ib) so += P.part[(o * P.nb + ib) * P.RP + p];
+        if (P.tail) {
+            // tiles split between two CTAs: add the part of the CTA whose range ends inside the tile
+            const int64_t U = P.n_tiles * P.upt;
+            for (int64_t ib = 0; ib < P.nb; ++ib) {
+                const int64_t ua = (o * P.nb + ib) * P.upt, ub = ua + P.upt - 1;
+                const int ga = (int)(((ua + 1) * P.G - 1) / U), gb = (int)(((ub + 1) * P.G - 1) / U);
+                if (ga != gb) so += P.tail[(int64_t)ga * P.RP + p];
+            }
         }
-    return s;
-}
-
-// Last mode: one partial per streaming CTA along the tile axis.
-__device__ __forceinline__ float reduce_last(const ReduceParams& P, int64_t c, int p) {
-    float s = 0.f;
-    const float* q = P.part + c * P.RP + p;
-    const int64_t stride = P.Cpad * P.RP;
-    for (int g = 0; g < P.G; g += 16) {
-        float x[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) x[u] = (g + u < P.G) ? q[(int64_t)(g + u) * stride] : 0.f;
-#pragma unroll
-        for (int u = 0; u < 16; ++u) s += x[u];
+        s = fmaf(P.W[o * P.RP + p], so, s);
     }
     return s;
 }
 
+// Last mode: one partial per streaming CTA along the tile axis.
+__device__ __forceinline__ float reduce_last(const ReduceParams& P, int64_t c, int p, int h, int H) {
+    const int ga = (P.G * h) / H, gb = (P.G * (h + 1)) / H;
+    float s = 0.f;
+    const float* q = P.part + c * P.RP + p;
+    const int64_t stride = P.Cpad * P.RP;
+    for (int g = ga; g < gb; g += 32) {
+        float x[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) x[u] = (g + u < gb) ? q[(int64_t)(g + u) * stride] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 32; ++u) s += x[u];
+    }
+    return s;
+}
+
+// piece h of H of M(j, p)
+__device__ __forceinline__ float reduce_piece(const ReduceParams& P, int64_t j, int p, int h, int H) {
+    return P.kind == 0 ? reduce_inner(P, j, p, h, H) : P.kind == 1 ? reduce_outer(P, j, p, h, H)
+                                                                   : reduce_last(P, j, p, h, H);
+}
+
 __device__ __forceinline__ float reduce_output(const ReduceParams& P, int64_t j, int p) {
-    return P.kind == 0 ? reduce_inner(P, j, p) : P.kind == 1 ? reduce_outer(P, j, p) : reduce_last(P, j, p);
+    return reduce_piece(P, j, p, 0, 1);
 }
 #endif
 

@@ -126,7 +126,7 @@ __device__ __forceinline__ void read_rows(uint32_t tmem_row, int col0, float (&y
 // rows kernel (inner / outer modes)
 // ----------------------------------------------------------------------------
 template <int RPH, bool INNER>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
     constexpr int N = 2 * RPH;
     constexpr int kB = N * 128;                 // factor chunk: N rows x 64 bf16 (swizzled)
     constexpr int kStage = kBoxBytes + kB;      // multiple of 1024 (N multiple of 16)
@@ -146,8 +146,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_rows(const __grid_constant
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = blockIdx.x, G = gridDim.x;
-    int64_t t_beg, t_end;
-    tile_range(P.n_tiles, g, G, t_beg, t_end);
+    // this CTA's work units (64-column chunks of tiles), a contiguous range: every CTA
+    // streams the same number of bytes, give or take one chunk
+    int64_t u_beg, u_end;
+    tile_range(P.n_tiles * P.upt, g, G, u_beg, u_end);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcStages; ++s) {
@@ -166,6 +168,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_rows(const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();
+    pdl_trigger();
 
     if (warp == 4) {
         // ------------------------------ producer ------------------------------
@@ -175,23 +179,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_rows(const __grid_constant
             uint32_t phase = 0;
             int64_t issued = 0;
             bool ok = true;
-            for (int64_t t = t_beg; t < t_end && ok; ++t) {
+            for (int64_t u = u_beg; u < u_end; ++u) {
+                const int64_t t = u / P.upt;
+                const int kc = (int)(u - t * P.upt);
                 int64_t ib, ot;
                 if (INNER) { ib = t / P.n_ot; ot = t % P.n_ot; }
                 else { ot = t / P.nb; ib = t % P.nb; }
-                for (int kc = 0; kc < P.n_kc; ++kc) {
-                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
-                        record_device_error(P.err, kErrWaitEmpty);
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_expect_tx(&full[stage], (uint32_t)kStage);
-                    unsigned char* st = base_ptr + stage * kStage;
-                    tma_load_3d(st, &tmap, &full[stage], kc * 64, (int)(ib * P.I_T), (int)(ot * P.O_T));
-                    bulk_load(st + kBoxBytes, P.FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
-                    ++issued;
-                    if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
+                if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
+                    record_device_error(P.err, kErrWaitEmpty);
+                    ok = false;
+                    break;
                 }
+                mbar_arrive_expect_tx(&full[stage], (uint32_t)kStage);
+                unsigned char* st = base_ptr + stage * kStage;
+                tma_load_3d(st, &tmap, &full[stage], kc * 64, (int)(ib * P.I_T), (int)(ot * P.O_T));
+                bulk_load(st + kBoxBytes, P.FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
+                ++issued;
+                if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
             }
             drain_stages(full, stage, phase, issued, P.err);
         }
@@ -205,8 +209,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_rows(const __grid_constant
             uint32_t phase = 0;
             bool ok = true;
             int64_t gq = 0;   // accumulator (chunk) counter of this CTA
-            for (int64_t t = t_beg; t < t_end && ok; ++t) {
-                for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
+            for (int64_t u = u_beg; u < u_end; ++u, ++gq) {
+                {
                     const int d = (int)(gq % kDbuf);
                     if (!mbar_wait_bounded(&tempty[d], (uint32_t)((gq / kDbuf) & 1) ^ 1u) ||
                         !mbar_wait_bounded(&full[stage], phase)) {
@@ -265,10 +269,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_rows(const __grid_constant
 #pragma unroll
         for (int p = 0; p < RPH; ++p) macc[p] = 0.f;
     };
-    for (int64_t t = t_beg; t < t_end; ++t) {
+    const int64_t t_first = u_beg / P.upt;
+    const int64_t t_stop = u_end > u_beg ? (u_end - 1) / P.upt + 1 : t_first;
+    for (int64_t t = t_first; t < t_stop; ++t) {
         int64_t ib, ot;
         if (INNER) { ib = t / P.n_ot; ot = t % P.n_ot; }
         else { ot = t / P.nb; ib = t % P.nb; }
+        // the chunks of tile t in this CTA's range
+        const int kc_lo = (int)(u_beg > t * P.upt ? u_beg - t * P.upt : 0);
+        const int kc_hi = (int)(u_end < (t + 1) * P.upt ? u_end - t * P.upt : P.upt);
         if (INNER && ib != cur_ib) {
             if (cur_ib >= 0) flush_inner(seg++);
             cur_ib = ib;
@@ -293,7 +302,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_rows(const __grid_constant
         float y[RPH];
 #pragma unroll
         for (int p = 0; p < RPH; ++p) y[p] = 0.f;
-        for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
+        for (int kc = kc_lo; kc < kc_hi; ++kc, ++gq) {
             const int d = (int)(gq % kDbuf);
             if (ok && !warp_wait(&tfull[d], (uint32_t)((gq / kDbuf) & 1))) {
                 if (lane == 0) record_device_error(P.err, kErrWaitFull);
@@ -330,7 +339,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_rows(const __grid_constant
             named_bar_sync(1, 128);
             if (warp == 0 && lane < P.r && ok) {
                 const float s4 = (zs[lane] + zs[32 + lane]) + (zs[64 + lane] + zs[96 + lane]);
-                P.part[((ot * P.nb) + ib) * P.RP + lane] = s4;
+                // the CTA holding the tile's last chunk writes the tile's slot; a range that
+                // ends inside the tile leaves its part in the CTA's tail slot
+                if (kc_hi == P.upt) P.part[((ot * P.nb) + ib) * P.RP + lane] = s4;
+                else P.tail[(int64_t)g * P.RP + lane] = s4;
             }
             parity ^= 1;
         }
@@ -390,6 +402,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_wait();
+    pdl_trigger();
 
     if (warp == 4) {
         if (lane == 0) {
@@ -500,7 +514,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
 
 template <int RPH>
 cudaError_t launch_tc_impl(int kind, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
-                           const TcParams& P) {
+                           const TcParams& P, bool pdl) {
     typedef void (*Kern)(const CUtensorMap, const TcParams);
     Kern k = kind == 0 ? (Kern)k_tc_rows<RPH, true> : kind == 1 ? (Kern)k_tc_rows<RPH, false> : (Kern)k_tc_last<RPH>;
     static size_t set_bytes[3] = {0, 0, 0};
@@ -510,8 +524,7 @@ cudaError_t launch_tc_impl(int kind, dim3 grid, size_t smem, cudaStream_t st, co
         set_bytes[kind] = smem;
     }
     if (grid.x == 0) return cudaSuccess;
-    k<<<grid, kTcThreads, smem, st>>>(map, P);
-    return cudaGetLastError();
+    return launch_kernel(k, grid, dim3(kTcThreads), smem, st, pdl, map, P);
 }
 
 }  // namespace
@@ -529,12 +542,12 @@ size_t tc_last_smem(int rph) {
 size_t tc_last_b_bytes(int rph) { return (size_t)2 * (2 * rph) * 128; }
 
 cudaError_t launch_stream_tc(int kind, int rph, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
-                             const TcParams& P) {
+                             const TcParams& P, bool pdl) {
     switch (rph) {
-        case 8: return launch_tc_impl<8>(kind, grid, smem, st, map, P);
-        case 16: return launch_tc_impl<16>(kind, grid, smem, st, map, P);
-        case 24: return launch_tc_impl<24>(kind, grid, smem, st, map, P);
-        case 32: return launch_tc_impl<32>(kind, grid, smem, st, map, P);
+        case 8: return launch_tc_impl<8>(kind, grid, smem, st, map, P, pdl);
+        case 16: return launch_tc_impl<16>(kind, grid, smem, st, map, P, pdl);
+        case 24: return launch_tc_impl<24>(kind, grid, smem, st, map, P, pdl);
+        case 32: return launch_tc_impl<32>(kind, grid, smem, st, map, P, pdl);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -10,6 +10,7 @@ struct TcParams {
     int I_T, O_T;
     int64_t nb, n_ot, n_tiles;
     int n_kc;
+    int upt;                    // rows kernels: work units (64-column chunks) per tile
     int RP, r;
     int Smax;
     int64_t Cpad;
@@ -18,6 +19,7 @@ struct TcParams {
     const float* Fi;            // packed A_{N-2}: Ii x RP (fp32)
     const float* W;             // n_o x RP (fp32)
     float* part;
+    float* tail;                // outer mode: G x RP, the tile a CTA's range ends inside (or nullptr)
     int* err;
 };
 
@@ -25,6 +27,6 @@ size_t tc_rows_smem(int rph);
 size_t tc_last_smem(int rph);
 size_t tc_last_b_bytes(int rph);
 cudaError_t launch_stream_tc(int kind, int rph, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
-                             const TcParams& P);
+                             const TcParams& P, bool pdl = false);
 
 }  // namespace ntf

@@ -10,6 +10,7 @@
 
 #include <atomic>
 #include <string>
+#include <utility>
 
 #include "../../include/ntf.h"
 
@@ -56,6 +57,18 @@ inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialisation attribute may start while its predecessor in the
+// stream is still running; pdl_wait() returns once the predecessor has
+// completed and its memory operations are visible, so every kernel on the
+// fused path calls it before touching anything another kernel wrote.  After
+// the wait it lets its own successor launch (pdl_trigger); the successor then
+// waits in turn, so at most two consecutive kernels are resident and no
+// kernel reads data before its producer has finished.  Without the attribute
+// both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ uint64_t global_timer_ns() {
     uint64_t t;
@@ -146,5 +159,24 @@ __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w 
 ntf_status encode_tensor_map_3d(CUtensorMap* map, ntf_dtype dtype, const void* base, uint64_t d0, uint64_t d1,
                                 uint64_t d2, uint64_t stride1_bytes, uint64_t stride2_bytes, uint32_t box0,
                                 uint32_t box1, uint32_t box2);
+
+#ifdef __CUDACC__
+// launch with or without the programmatic stream-serialisation attribute
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                 bool pdl, Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+#endif
 
 }  // namespace ntf

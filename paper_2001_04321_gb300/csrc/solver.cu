@@ -5,6 +5,8 @@
 #include "small.cuh"
 #include "epilogue.cuh"
 
+#include <cstdlib>
+
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -44,8 +46,14 @@ struct Solver {
     std::vector<void*> allocs;
     int iters_done = 0;
     double seconds = 0.0;
-    // timing of the streaming kernels
+    // timing of the streaming kernels: every timing_every-th iteration has CUDA
+    // events around its streaming launches (0 = off)
     bool timing = false;
+    int timing_every = 0;
+    int64_t iter_seq = 0;      // iterations issued (eagerly or into the graph being captured)
+    bool timed_now = false;    // the iteration being issued is timed
+    // programmatic dependent launch on the fused path (off with NTF_PDL=0)
+    bool pdl = true;
     std::vector<StreamTimer> ev;
     size_t ev_used = 0;
     // fused main path (HALS, one sweep, rank <= 32)
@@ -58,7 +66,7 @@ struct Solver {
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
     int g_iters = 0;
-    bool g_timing = false;
+    int g_timing = 0;          // timing_every the graph was captured with
     int64_t g_kernels = 0;   // kernel nodes in the graph
 
     ~Solver() {
@@ -83,7 +91,7 @@ struct Solver {
     }
 
     StreamTimer* next_timer() {
-        if (!timing) return nullptr;
+        if (!timing || !timed_now) return nullptr;
         if (ev_used == ev.size()) {
             StreamTimer t;
             if (cudaEventCreate(&t.start) != cudaSuccess || cudaEventCreate(&t.stop) != cudaSuccess) {
@@ -165,9 +173,11 @@ struct Solver {
             pp.fin_blocks = epilogue_blocks(vs.dims[pp.fin_mode]);
             pp.gpart = gpart;
             pp.her = use_her ? her : nullptr;
-            cudaError_t e = launch_prep(pp, st);
+            cudaError_t e = launch_prep(pp, st, pdl);
             if (e != cudaSuccess) return cuda_fail(e, "prep");
-            ntf_status s = run_mttkrp_stream(vs, P, ws_mt, st, &tm[n], next_timer());
+            // a kernel right after an event record is launched without the PDL attribute
+            StreamTimer* timer = next_timer();
+            ntf_status s = run_mttkrp_stream(vs, P, ws_mt, st, &tm[n], timer, pdl);
             if (s != NTF_OK) return s;
             EpiParams ep{};
             ep.B = fb;
@@ -189,7 +199,7 @@ struct Solver {
             ep.fhat_out = &scal[1];
             ep.iters_out = iters_dev;
             ep.her = use_her ? her : nullptr;
-            e = launch_epilogue(ep, st);
+            e = launch_epilogue(ep, st, pdl && !timer);
             if (e != cudaSuccess) return cuda_fail(e, "epilogue");
         }
         return NTF_OK;
@@ -206,6 +216,8 @@ struct Solver {
 
     // one outer iteration of Alg. 2 (or Alg. 1 when her == 0)
     ntf_status iterate(cudaStream_t st) {
+        timed_now = timing_every > 0 && (iter_seq % timing_every) == 0;
+        ++iter_seq;
         if (fused) return iterate_fused(st);
         const bool use_her = o.her != 0;
         for (int n = 0; n < N; ++n) {
@@ -315,6 +327,10 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     if (opts) S->o = *opts;
     else ntf_opts_default(&S->o);
     s = validate_opts(S->o);
+    {
+        const char* e = std::getenv("NTF_PDL");
+        S->pdl = !(e && e[0] == '0');
+    }
     if (s != NTF_OK) return bail(s);
     S->N = S->vu.order;
     S->r = rank;
@@ -419,6 +435,7 @@ static ntf_status capture_graph(Solver* S, int iters, cudaStream_t st) {
         S->gexec = nullptr;
     }
     S->ev_used = 0;   // the graph's event records use the first timers of the pool
+    S->iter_seq = 0;  // the graph's first iteration is timed (when timing is on)
     cudaGraph_t g;
     const int64_t before = ntf_launch_count();
     NTF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -435,7 +452,7 @@ static ntf_status capture_graph(Solver* S, int iters, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     S->gstream = st;
     S->g_iters = iters;
-    S->g_timing = S->timing;
+    S->g_timing = S->timing_every;
     return NTF_OK;
 }
 
@@ -455,7 +472,7 @@ static ntf_status run_solver(Solver* S, int iters, cudaStream_t st) {
     int left = iters;
     while (left > 0) {
         const int chunk = left < kMaxGraphIters ? left : kMaxGraphIters;
-        if (!S->gexec || S->gstream != st || S->g_iters != chunk || S->g_timing != S->timing) {
+        if (!S->gexec || S->gstream != st || S->g_iters != chunk || S->g_timing != S->timing_every) {
             ntf_status s = capture_graph(S, chunk, st);
             if (s != NTF_OK) return s;
         }
@@ -547,7 +564,8 @@ ntf_status ntf_solver_prepare_graph(ntf_solver* h, int iters, void* stream) {
 
 ntf_status ntf_solver_set_timing(ntf_solver* h, int on) {
     if (!h || !h->s) return fail(NTF_EINVAL, "solver is NULL");
-    h->s->timing = on != 0;
+    h->s->timing_every = on > 0 ? on : 0;
+    h->s->timing = on > 0;
     if (!h->s->gexec) h->s->ev_used = 0;
     return NTF_OK;
 }
