@@ -72,6 +72,7 @@ __global__ void k_prep(const PrepParams P) {
     const int rr = P.r * P.r;
     const int n = P.mode;
     const FusedBufs& B = P.B;
+    if (P.sched && blockIdx.x == 0 && threadIdx.x == 0) *P.sched = 0u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // Control words first, all loads in flight together: the current buffer of
     // every mode (lane l holds mode l's), the iteration count and the last decision.

@@ -33,6 +33,7 @@ struct PrepParams {
     int RPH, n_kc;                      // n_kc: 64-row chunks of FcT
     float* Fi;                          // packed second-to-last factor (FFMA stream), or nullptr
     float* W;                           // weight table
+    unsigned int* sched;                // tile counter of the next stream (set to 0 here), or nullptr
     // Grams of the mode updated just before (fin_mode) are finished here from the
     // epilogue partials; for mode 0 that is the last mode of the previous iteration
     int fin_mode, fin_blocks;

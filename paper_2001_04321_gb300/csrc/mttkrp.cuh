@@ -35,11 +35,10 @@ struct MttkrpPlan {
     int G;               // streaming CTAs along the tile axis
     int n_cb;            // last mode: 64-column blocks
     int Smax;
-    int upt;             // work units per tile: CTAs own contiguous ranges of units (tensor-core row
-                         // kernels: one unit per 64-column chunk, so CTAs get equal bytes; else 1)
+    bool tile_slots;     // one partial-sum slot per tile (tensor-core row kernels, scheduled at run time)
     int64_t Cpad;
     // workspace layout (byte offsets)
-    size_t off_Fc, off_Fi, off_W, off_part, off_tail, total;   // off_Fc holds FcT (bf16) on the tc path
+    size_t off_Fc, off_Fi, off_W, off_part, off_sched, total;   // off_Fc holds FcT (bf16) on the tc path
 };
 
 ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* plan);

@@ -133,7 +133,9 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     P.tc = v.dtype == NTF_BF16 && rank <= 32;
     P.RPH = (int)round_up(rank, 8);
     P.kind = mode == v.order - 1 ? ModeKind::Last : mode == v.order - 2 ? ModeKind::Inner : ModeKind::Outer;
-    if (P.kind == ModeKind::Inner) choose_tile(v.Ii, v.n_o, 32, false, &P.I_T, &P.O_T);
+    // inner mode: the tensor-core kernel keeps one slot per tile, so the smallest inner
+    // extent (fewest tiles per output row) is preferred; the FFMA kernel the largest
+    if (P.kind == ModeKind::Inner) choose_tile(v.Ii, v.n_o, 32, P.tc, &P.I_T, &P.O_T);
     else if (P.kind == ModeKind::Outer || P.tc) { P.I_T = 128; P.O_T = 1; }   // tc last mode: W(o,:) per tile
     else choose_tile(v.Ii, v.n_o, 128, false, &P.I_T, &P.O_T);
     P.nb = ceil_div(v.Ii, P.I_T);
@@ -153,16 +155,15 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
         const int per_sm = (P.tc && 2 * tc_rows_smem(P.RPH) <= 227 * 1024) ? 2 : 1;
         P.G = (int)std::min<int64_t>(P.n_tiles, (int64_t)sms * per_sm);
     }
-    // tensor-core row kernels split the work at 64-column chunks (a tile then meets at most
-    // two CTAs, since G <= n_tiles); the others at whole tiles
-    P.upt = (P.tc && P.kind != ModeKind::Last) ? P.n_kc : 1;
+    // tensor-core row kernels take tiles at run time and keep one slot per tile; the
+    // others own contiguous tile ranges and keep one slot per (CTA, segment)
+    P.tile_slots = P.tc && P.kind != ModeKind::Last;
     P.Smax = 1;
-    if (P.kind == ModeKind::Inner) {
-        const int64_t U = P.n_tiles * P.upt;
+    if (P.kind == ModeKind::Inner && !P.tile_slots) {
         for (int g = 0; g < P.G; ++g) {
-            const int64_t b = (U * g) / P.G, e = (U * (g + 1)) / P.G;
+            const int64_t b = (P.n_tiles * g) / P.G, e = (P.n_tiles * (g + 1)) / P.G;
             if (e > b) {
-                const int s = (int)(((e - 1) / P.upt) / P.n_ot - (b / P.upt) / P.n_ot + 1);
+                const int s = (int)((e - 1) / P.n_ot - b / P.n_ot + 1);
                 if (s > P.Smax) P.Smax = s;
             }
         }
@@ -182,15 +183,16 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     P.off_part = off;
     size_t part = 0;
     if (P.kind == ModeKind::Inner)
-        part = (size_t)P.G * P.Smax * (P.tc ? 1 : kStreamWarps) * P.I_T * P.RP;
+        part = P.tile_slots ? (size_t)P.n_tiles * P.I_T * P.RP
+                            : (size_t)P.G * P.Smax * kStreamWarps * P.I_T * P.RP;
     else if (P.kind == ModeKind::Outer)
         part = (size_t)v.n_o * P.nb * P.RP;
     else
         part = (size_t)P.G * P.Cpad * P.RP;
     off = align256(off + sizeof(float) * part);
-    // outer mode with split tiles: the part of a tile held by the CTA whose range ends inside it
-    P.off_tail = off;
-    if (P.kind == ModeKind::Outer && P.upt > 1) off = align256(off + sizeof(float) * (size_t)P.G * P.RP);
+    // the run-time tile counter of the tensor-core row kernels
+    P.off_sched = off;
+    if (P.tile_slots) off = align256(off + sizeof(unsigned int));
     P.total = off;
     *p = P;
     return NTF_OK;
@@ -293,11 +295,8 @@ ReduceParams make_reduce_params(const TensorView& v, const MttkrpPlan& P, const 
     R.RP = P.RP;
     R.r = P.rank;
     R.part_warps = P.tc ? 1 : kStreamWarps;
-    R.upt = P.upt;
+    R.tile_slots = P.tile_slots ? 1 : 0;
     R.part = part;
-    R.tail = (P.kind == ModeKind::Outer && P.upt > 1)
-                 ? reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(part) + (P.off_tail - P.off_part))
-                 : nullptr;
     R.W = W;
     if (P.kind == ModeKind::Outer) {
         R.In = v.dims[P.mode];
@@ -385,8 +384,7 @@ ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* wor
         T.n_ot = P.n_ot;
         T.n_tiles = P.n_tiles;
         T.n_kc = P.n_kc;
-        T.upt = P.upt;
-        T.tail = (P.kind == ModeKind::Outer && P.upt > 1) ? reinterpret_cast<float*>(ws + P.off_tail) : nullptr;
+        T.sched = P.tile_slots ? reinterpret_cast<unsigned int*>(ws + P.off_sched) : nullptr;
         T.RP = P.RP;
         T.r = P.rank;
         T.Smax = P.Smax;
@@ -462,6 +460,7 @@ ntf_status run_mttkrp(const TensorView& v, const MttkrpPlan& P, const float* con
     }
 
     // 2. streaming kernel
+    if (P.tile_slots) NTF_CUDA_TRY(cudaMemsetAsync(ws + P.off_sched, 0, sizeof(unsigned int), st));
     ntf_status s = run_mttkrp_stream(v, P, workspace, st, cache, timer);
     if (s != NTF_OK) return s;
 

@@ -97,6 +97,18 @@ __device__ __forceinline__ bool warp_wait_bounded(uint64_t* bar, uint32_t parity
 
 // Producer drain: wait (bounded) until every copy this thread issued has
 // landed, so that no TMA write is in flight when the CTA retires.
+// acc[0..3] += a * (f.x, f.y, f.z, f.w) as two packed FP32x2 FMAs (each lane an
+// IEEE fma, round to nearest): half the FMA issue slots of four scalar FMAs
+__device__ __forceinline__ void fma4(float* acc, float a, const float4& f) {
+    const float2 a2 = make_float2(a, a);
+    const float2 lo = __ffma2_rn(a2, make_float2(f.x, f.y), make_float2(acc[0], acc[1]));
+    const float2 hi = __ffma2_rn(a2, make_float2(f.z, f.w), make_float2(acc[2], acc[3]));
+    acc[0] = lo.x;
+    acc[1] = lo.y;
+    acc[2] = hi.x;
+    acc[3] = hi.y;
+}
+
 __device__ __forceinline__ void drain_stages(uint64_t* full, int stage, uint32_t phase, int64_t issued, int* err) {
     const int64_t inflight = issued < kStreamStages ? issued : kStreamStages;
     for (int64_t q = 0; q < inflight; ++q) {
@@ -251,12 +263,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                             for (int p = 0; p < R; p += 4) {
                                 const float4 f = lds128f(frow + p * 4);
 #pragma unroll
-                                for (int j = 0; j < 4; ++j) {
-                                    acc[j][p + 0] = fmaf(tv[j][kk], f.x, acc[j][p + 0]);
-                                    acc[j][p + 1] = fmaf(tv[j][kk], f.y, acc[j][p + 1]);
-                                    acc[j][p + 2] = fmaf(tv[j][kk], f.z, acc[j][p + 2]);
-                                    acc[j][p + 3] = fmaf(tv[j][kk], f.w, acc[j][p + 3]);
-                                }
+                                for (int j = 0; j < 4; ++j) fma4(acc[j] + p, tv[j][kk], f);
                             }
                         }
                     }
@@ -279,12 +286,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                         for (int p = 0; p < R; p += 4) {
                             const float4 f = lds128f(frow + p * 4);
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                acc[j][p + 0] = fmaf(tv[j], f.x, acc[j][p + 0]);
-                                acc[j][p + 1] = fmaf(tv[j], f.y, acc[j][p + 1]);
-                                acc[j][p + 2] = fmaf(tv[j], f.z, acc[j][p + 2]);
-                                acc[j][p + 3] = fmaf(tv[j], f.w, acc[j][p + 3]);
-                            }
+                            for (int j = 0; j < 4; ++j) fma4(acc[j] + p, tv[j], f);
                         }
                     }
                 }
@@ -494,12 +496,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 for (int p = 0; p < R; p += 4) {
                     const float4 f = lds128f(krow + p * 4);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        acc[c][p + 0] = fmaf(tv[c], f.x, acc[c][p + 0]);
-                        acc[c][p + 1] = fmaf(tv[c], f.y, acc[c][p + 1]);
-                        acc[c][p + 2] = fmaf(tv[c], f.z, acc[c][p + 2]);
-                        acc[c][p + 3] = fmaf(tv[c], f.w, acc[c][p + 3]);
-                    }
+                    for (int c = 0; c < 4; ++c) fma4(acc[c] + p, tv[c], f);
                 }
             }
         }

@@ -12,11 +12,10 @@ struct ReduceParams {
     int64_t n_tiles, n_ot, nb, Ii, n_o, C, Cpad;
     int G, Smax, I_T, RP, r;
     int part_warps;               // inner mode: partial slots per CTA (8 per-warp, or 1)
-    int upt;                      // work units per tile (CTAs own contiguous unit ranges)
+    int tile_slots;               // inner mode: one slot per tile instead of per (CTA, segment)
     int64_t In, stride, hi_count;  // outer mode: o = (hi*In + j)*stride + lo
     const float* part;
     const float* W;
-    const float* tail;            // outer mode, split tiles: per-CTA part of the tile its range ends in
 };
 
 #ifdef __CUDACC__
@@ -31,15 +30,29 @@ struct ReduceParams {
 __device__ __forceinline__ float reduce_inner(const ReduceParams& P, int64_t j, int p, int h, int H) {
     const int64_t ib = j / P.I_T;
     const int b = (int)(j % P.I_T);
-    // units (upt per tile) of block ib: [u0, u1).  CTA g owns units [floor(U g / G),
-    // floor(U (g+1) / G)); the CTA owning unit u is floor(((u + 1) G - 1) / U)
-    const int64_t U = P.n_tiles * P.upt;
-    const int64_t u0 = ib * P.n_ot * P.upt, u1 = u0 + P.n_ot * P.upt;
-    const int g0 = (int)(((u0 + 1) * P.G - 1) / U);
-    const int g1 = (int)((u1 * P.G - 1) / U);
+    if (P.tile_slots) {
+        // one slot per tile (ib, ot): sum over the n_ot tiles of block ib
+        const int64_t oa = (P.n_ot * h) / H, ob = (P.n_ot * (h + 1)) / H;
+        const float* q = P.part + ((ib * P.n_ot) * P.I_T + b) * P.RP + p;
+        const int64_t tstride = (int64_t)P.I_T * P.RP;
+        float s = 0.f;
+        for (int64_t o = oa; o < ob; o += 32) {
+            float x[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) x[u] = (o + u < ob) ? q[(o + u) * tstride] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 32; ++u) s += x[u];
+        }
+        return s;
+    }
+    const int64_t t0 = ib * P.n_ot, t1 = t0 + P.n_ot;   // tiles of block ib
+    // CTA g owns tiles [floor(n_tiles g / G), floor(n_tiles (g+1) / G)); the CTA owning tile t is
+    // floor(((t + 1) G - 1) / n_tiles)
+    const int g0 = (int)(((t0 + 1) * P.G - 1) / P.n_tiles);
+    const int g1 = (int)((t1 * P.G - 1) / P.n_tiles);
     // CTA g0 may have started in an earlier block (segment ib - its first block); every later
     // CTA that meets block ib starts inside it (segment 0)
-    const int seg0 = (int)(ib - (((U * g0) / P.G) / P.upt) / P.n_ot);
+    const int seg0 = (int)(ib - ((P.n_tiles * g0) / P.G) / P.n_ot);
     const int cnt = g1 - g0 + 1;
     const int ga = g0 + (cnt * h) / H, gb = g0 + (cnt * (h + 1)) / H;   // this piece: CTAs [ga, gb)
     const int64_t slot = (int64_t)P.part_warps * P.I_T * P.RP;          // one (CTA, segment) slot
@@ -88,15 +101,6 @@ __device__ __forceinline__ float reduce_outer(const ReduceParams& P, int64_t j, 
         float so = 0.f;
 #pragma unroll 4
         for (int64_t ib = 0; ib < P.nb; ++ib) so += P.part[(o * P.nb + ib) * P.RP + p];
-        if (P.tail) {
-            // tiles split between two CTAs: add the part of the CTA whose range ends inside the tile
-            const int64_t U = P.n_tiles * P.upt;
-            for (int64_t ib = 0; ib < P.nb; ++ib) {
-                const int64_t ua = (o * P.nb + ib) * P.upt, ub = ua + P.upt - 1;
-                const int ga = (int)(((ua + 1) * P.G - 1) / U), gb = (int)(((ub + 1) * P.G - 1) / U);
-                if (ga != gb) so += P.tail[(int64_t)ga * P.RP + p];
-            }
-        }
         s = fmaf(P.W[o * P.RP + p], so, s);
     }
     return s;

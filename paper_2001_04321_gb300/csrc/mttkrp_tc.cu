@@ -124,7 +124,16 @@ __device__ __forceinline__ void read_rows(uint32_t tmem_row, int col0, float (&y
 
 // ----------------------------------------------------------------------------
 // rows kernel (inner / outer modes)
+//
+// Tiles are handed out at run time: the producer takes the next tile index
+// from a device counter (reset before every launch) and passes it to the MMA
+// warp and the epilogue warps through a small ring guarded by its own pair of
+// mbarriers.  Every tile writes its own output slot, so the result does not
+// depend on which CTA took which tile, and CTAs that stream faster take more
+// tiles (no tail of slow CTAs).
 // ----------------------------------------------------------------------------
+constexpr int kTileRing = 4;
+
 template <int RPH, bool INNER>
 __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
     constexpr int N = 2 * RPH;
@@ -140,16 +149,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
     uint64_t* tfull = empty + kTcStages;        // [kDbuf]: accumulator of one 64-column chunk ready
     uint64_t* tempty = tfull + kDbuf;           // [kDbuf]: accumulator read by the epilogue
     uint64_t* drain = tempty + kDbuf;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* sfull = drain + 1;                // [kTileRing]: tile index published
+    uint64_t* sempty = sfull + kTileRing;       // [kTileRing]: tile index read by all consumers
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + kTileRing);
+    int* tile_ring = reinterpret_cast<int*>(tmem_slot + 1);                          // [kTileRing]
     float* zsum = reinterpret_cast<float*>(base_ptr + kTcStages * kStage + 256);   // [2][4][32]
     float* red = zsum + 2 * 4 * 32;                                                  // [128][RPH]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = blockIdx.x, G = gridDim.x;
-    // this CTA's work units (64-column chunks of tiles), a contiguous range: every CTA
-    // streams the same number of bytes, give or take one chunk
-    int64_t u_beg, u_end;
-    tile_range(P.n_tiles * P.upt, g, G, u_beg, u_end);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTcStages; ++s) {
@@ -161,6 +168,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
             mbar_init(&tempty[b], 4);
         }
         mbar_init(drain, 1);
+        for (int k = 0; k < kTileRing; ++k) {
+            mbar_init(&sfull[k], 1);
+            mbar_init(&sempty[k], 5);           // the MMA thread and the 4 epilogue warps
+        }
         fence_mbar_init();
     }
     if (warp == 5) tmem_alloc(tmem_slot, 64 * kDbuf);
@@ -172,30 +183,41 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
     pdl_trigger();
 
     if (warp == 4) {
-        // ------------------------------ producer ------------------------------
+        // ------------------------- scheduler + producer -------------------------
         if (lane == 0) {
             prefetch_tensormap(&tmap);
             int stage = 0;
             uint32_t phase = 0;
             int64_t issued = 0;
-            bool ok = true;
-            for (int64_t u = u_beg; u < u_end; ++u) {
-                const int64_t t = u / P.upt;
-                const int kc = (int)(u - t * P.upt);
+            for (int64_t s = 0;; ++s) {
+                const int slot = (int)(s % kTileRing);
+                if (!mbar_wait_bounded(&sempty[slot], (uint32_t)((s / kTileRing) & 1) ^ 1u)) {
+                    record_device_error(P.err, kErrWaitEmpty);
+                    break;
+                }
+                const unsigned int grab = atomicAdd(P.sched, 1u);
+                const int t = grab < (unsigned int)P.n_tiles ? (int)grab : -1;
+                tile_ring[slot] = t;
+                mbar_arrive(&sfull[slot]);              // releases the slot to the consumers
+                if (t < 0) break;
                 int64_t ib, ot;
                 if (INNER) { ib = t / P.n_ot; ot = t % P.n_ot; }
                 else { ot = t / P.nb; ib = t % P.nb; }
-                if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
-                    record_device_error(P.err, kErrWaitEmpty);
-                    ok = false;
-                    break;
+                bool ok = true;
+                for (int kc = 0; kc < P.n_kc; ++kc) {
+                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
+                        record_device_error(P.err, kErrWaitEmpty);
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[stage], (uint32_t)kStage);
+                    unsigned char* st = base_ptr + stage * kStage;
+                    tma_load_3d(st, &tmap, &full[stage], kc * 64, (int)(ib * P.I_T), (int)(ot * P.O_T));
+                    bulk_load(st + kBoxBytes, P.FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
+                    ++issued;
+                    if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
                 }
-                mbar_arrive_expect_tx(&full[stage], (uint32_t)kStage);
-                unsigned char* st = base_ptr + stage * kStage;
-                tma_load_3d(st, &tmap, &full[stage], kc * 64, (int)(ib * P.I_T), (int)(ot * P.O_T));
-                bulk_load(st + kBoxBytes, P.FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
-                ++issued;
-                if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
+                if (!ok) break;
             }
             drain_stages(full, stage, phase, issued, P.err);
         }
@@ -207,10 +229,18 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            bool ok = true;
             int64_t gq = 0;   // accumulator (chunk) counter of this CTA
-            for (int64_t u = u_beg; u < u_end; ++u, ++gq) {
-                {
+            bool ok = true;
+            for (int64_t s = 0; ok; ++s) {
+                const int slot = (int)(s % kTileRing);
+                if (!mbar_wait_bounded(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
+                    record_device_error(P.err, kErrWaitFull);
+                    break;
+                }
+                const int t = tile_ring[slot];
+                mbar_arrive(&sempty[slot]);
+                if (t < 0) break;
+                for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
                     const int d = (int)(gq % kDbuf);
                     if (!mbar_wait_bounded(&tempty[d], (uint32_t)((gq / kDbuf) & 1) ^ 1u) ||
                         !mbar_wait_bounded(&full[stage], phase)) {
@@ -245,43 +275,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
     // ------------------------------ epilogue (warps 0-3) ------------------------------
     const int m = threadIdx.x;                       // tile row = TMEM lane
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
-    float macc[RPH];
-#pragma unroll
-    for (int p = 0; p < RPH; ++p) macc[p] = 0.f;
-    int64_t cur_ib = -1;
-    int seg = 0;
     bool ok = true;
     int64_t gq = 0;
     int parity = 0;
-    auto flush_inner = [&](int s) {
-        // rows m, m + I_T, ... share inner row b = m % I_T of the block
-#pragma unroll
-        for (int p = 0; p < RPH; ++p) red[m * RPH + p] = macc[p];
-        named_bar_sync(1, 128);
-        if (m < P.I_T) {
-            for (int p = 0; p < P.r; ++p) {
-                float sacc = 0.f;
-                for (int a = 0; a < P.O_T; ++a) sacc += red[(a * P.I_T + m) * RPH + p];
-                P.part[(((int64_t)g * P.Smax + s) * P.I_T + m) * P.RP + p] = sacc;
-            }
+    for (int64_t s = 0; ok; ++s) {
+        const int slot = (int)(s % kTileRing);
+        if (!warp_wait(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
+            if (lane == 0) record_device_error(P.err, kErrWaitFull);
+            break;
         }
-        named_bar_sync(1, 128);
-#pragma unroll
-        for (int p = 0; p < RPH; ++p) macc[p] = 0.f;
-    };
-    const int64_t t_first = u_beg / P.upt;
-    const int64_t t_stop = u_end > u_beg ? (u_end - 1) / P.upt + 1 : t_first;
-    for (int64_t t = t_first; t < t_stop; ++t) {
+        const int t = tile_ring[slot];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sempty[slot]);
+        if (t < 0) break;
         int64_t ib, ot;
         if (INNER) { ib = t / P.n_ot; ot = t % P.n_ot; }
         else { ot = t / P.nb; ib = t % P.nb; }
-        // the chunks of tile t in this CTA's range
-        const int kc_lo = (int)(u_beg > t * P.upt ? u_beg - t * P.upt : 0);
-        const int kc_hi = (int)(u_end < (t + 1) * P.upt ? u_end - t * P.upt : P.upt);
-        if (INNER && ib != cur_ib) {
-            if (cur_ib >= 0) flush_inner(seg++);
-            cur_ib = ib;
-        }
         // weights of this row, fetched while the tile is being contracted
         float w[RPH];
         bool row_live;
@@ -302,7 +311,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
         float y[RPH];
 #pragma unroll
         for (int p = 0; p < RPH; ++p) y[p] = 0.f;
-        for (int kc = kc_lo; kc < kc_hi; ++kc, ++gq) {
+        for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
             const int d = (int)(gq % kDbuf);
             if (ok && !warp_wait(&tfull[d], (uint32_t)((gq / kDbuf) & 1))) {
                 if (lane == 0) record_device_error(P.err, kErrWaitFull);
@@ -320,8 +329,30 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
             }
         }
         if (INNER) {
+            // rows m = a I_T + b share inner row b of block ib: this tile's slot holds their
+            // weighted sum over the tile's O_T outer indices a.  Lanes with equal lane % I_T
+            // are summed by a butterfly, the 4 warps through shared memory, in a fixed order.
+            float z[RPH];
 #pragma unroll
-            for (int p = 0; p < RPH; ++p) macc[p] = fmaf(w[p], y[p], macc[p]);
+            for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
+            for (int off = 16; off >= P.I_T; off >>= 1)
+#pragma unroll
+                for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
+            // (I_T <= 32 divides 32: lane b of every warp now holds that warp's rows of b)
+            if (lane < P.I_T) {
+#pragma unroll
+                for (int p = 0; p < RPH; ++p) red[(warp * 32 + lane) * RPH + p] = z[p];
+            }
+            named_bar_sync(1, 128);
+            if (ok) {
+                for (int idx = m; idx < P.I_T * P.r; idx += 128) {
+                    const int b = idx / P.r, p = idx - b * P.r;
+                    const float sacc = (red[(0 * 32 + b) * RPH + p] + red[(1 * 32 + b) * RPH + p]) +
+                                       (red[(2 * 32 + b) * RPH + p] + red[(3 * 32 + b) * RPH + p]);
+                    P.part[((int64_t)t * P.I_T + b) * P.RP + p] = sacc;
+                }
+            }
+            named_bar_sync(1, 128);
         } else {
             float z[RPH];
 #pragma unroll
@@ -339,15 +370,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
             named_bar_sync(1, 128);
             if (warp == 0 && lane < P.r && ok) {
                 const float s4 = (zs[lane] + zs[32 + lane]) + (zs[64 + lane] + zs[96 + lane]);
-                // the CTA holding the tile's last chunk writes the tile's slot; a range that
-                // ends inside the tile leaves its part in the CTA's tail slot
-                if (kc_hi == P.upt) P.part[((ot * P.nb) + ib) * P.RP + lane] = s4;
-                else P.tail[(int64_t)g * P.RP + lane] = s4;
+                P.part[(int64_t)t * P.RP + lane] = s4;
             }
             parity ^= 1;
         }
     }
-    if (INNER && cur_ib >= 0) flush_inner(seg);
     tc_fence_before();
     named_bar_sync(2, 160);
 }

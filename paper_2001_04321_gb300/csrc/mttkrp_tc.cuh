@@ -10,7 +10,6 @@ struct TcParams {
     int I_T, O_T;
     int64_t nb, n_ot, n_tiles;
     int n_kc;
-    int upt;                    // rows kernels: work units (64-column chunks) per tile
     int RP, r;
     int Smax;
     int64_t Cpad;
@@ -18,8 +17,8 @@ struct TcParams {
                                 // block; N rows x 128 B per 64 rows, swizzled bf16 hi|lo
     const float* Fi;            // packed A_{N-2}: Ii x RP (fp32)
     const float* W;             // n_o x RP (fp32)
-    float* part;
-    float* tail;                // outer mode: G x RP, the tile a CTA's range ends inside (or nullptr)
+    float* part;                // rows kernels: one slot per tile; last kernel: one per CTA
+    unsigned int* sched;        // rows kernels: next tile to hand out (0 before every launch)
     int* err;
 };
 

@@ -169,6 +169,7 @@ struct Solver {
                         ? reinterpret_cast<float*>(ws + P.off_Fi)
                         : nullptr;
             pp.W = reinterpret_cast<float*>(ws + P.off_W);
+            pp.sched = P.tile_slots ? reinterpret_cast<unsigned int*>(ws + P.off_sched) : nullptr;
             pp.fin_mode = n > 0 ? n - 1 : N - 1;
             pp.fin_blocks = epilogue_blocks(vs.dims[pp.fin_mode]);
             pp.gpart = gpart;
