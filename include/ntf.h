@@ -321,8 +321,10 @@ typedef struct ntf_solver ntf_solver;
 NTF_API ntf_status ntf_solver_create(ntf_solver** out, const ntf_tensor* T, float* const* factors, int rank,
                              const ntf_opts* opts, void* stream);
 /* Run `iters` outer iterations on `stream` (asynchronous).  With opts.use_graph
- * and a non-default stream, iterations are captured once into CUDA graphs of up
- * to 1024 iterations and replayed. */
+ * and a non-default stream, a CUDA graph of 32 iterations is captured once and
+ * replayed (the remainder runs eagerly); a run whose length matches a graph made
+ * by ntf_solver_prepare_graph, or a timed run (at most 1024 iterations), replays
+ * one graph of all its iterations. */
 NTF_API ntf_status ntf_solver_run(ntf_solver* s, int iters, void* stream);
 /* With opts.use_graph: capture `iters` (1..1024) outer iterations into one CUDA
  * graph now, so that a later ntf_solver_run(s, iters, stream) on the same stream

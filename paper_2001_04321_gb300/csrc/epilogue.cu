@@ -214,8 +214,6 @@ cudaError_t launch_prep(const PrepParams& P, cudaStream_t st, bool pdl) {
 // epilogue
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) {
-    pdl_wait();
-    pdl_trigger();
     __shared__ float Vs[32 * 33];
     __shared__ float rinv[32];
     __shared__ float rowsA[kEpiRows][32];
@@ -226,20 +224,26 @@ __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = P.r, n = P.mode;
     const bool her = P.B.her != 0;
-    const int cn = P.B.cur[n];
+    const int rw = warp % kEpiRows, piece = warp / kEpiRows;
+    const int64_t row = (int64_t)blockIdx.x * kEpiRows + rw;
+    const bool live = row < P.rows && lane < r;
+    // Read before the wait for the stream: the current buffer index, the factor row,
+    // V and beta.  They were written two or more launches back, and this launch starts
+    // only after the stream's own wait has seen those launches complete.  Loads go to
+    // L2 (ld.global.cg), never to a possibly older L1 copy.
+    const int cn = __ldcg(P.B.cur + n);
     float* A = P.B.X[n][cn];                      // in: A_{k-1}, out: A_k
     float* Ah = her ? P.B.X[n][1 - cn] : nullptr; // out: A_hat_k
     for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
         const int l = q >> 5, c = q & 31;
-        Vs[l * 33 + c] = (l < r && c < r) ? P.Vf[l * r + c] : 0.f;
+        Vs[l * 33 + c] = (l < r && c < r) ? __ldcg(P.Vf + l * r + c) : 0.f;
     }
-    const float beta = her ? (float)*P.beta : 0.f;
+    const float beta = her ? (float)__ldcg(P.beta) : 0.f;
+    const float a_old = (live && piece == 0) ? __ldcg(A + row * r + lane) : 0.f;
+    pdl_wait();
+    pdl_trigger();
 
-    // M row pieces from the stream's partial sums, and the previous row
-    const int rw = warp % kEpiRows, piece = warp / kEpiRows;
-    const int64_t row = (int64_t)blockIdx.x * kEpiRows + rw;
-    const bool live = row < P.rows && lane < r;
-    const float a_old = (live && piece == 0) ? A[row * r + lane] : 0.f;
+    // M row pieces from the stream's partial sums
     float m = live ? reduce_piece(P.red, row, lane, piece, kEpiPieces) : 0.f;
     if (piece > 0) mpiece[piece - 1][rw][lane] = m;
     __syncthreads();

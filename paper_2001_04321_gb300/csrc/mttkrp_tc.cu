@@ -134,6 +134,18 @@ __device__ __forceinline__ void read_rows(uint32_t tmem_row, int col0, float (&y
 // ----------------------------------------------------------------------------
 constexpr int kTileRing = 4;
 
+// inner mode: tiles run over the inner blocks first; outer modes over the outer index first
+template <bool INNER>
+__device__ __forceinline__ void tile_coords(const TcParams& P, int64_t t, int64_t& ib, int64_t& ot) {
+    if (INNER) { ib = t / P.n_ot; ot = t % P.n_ot; }
+    else { ot = t / P.nb; ib = t % P.nb; }
+}
+
+// the statically assigned first tile of this CTA (-1 if there is none)
+__device__ __forceinline__ int g_first_tile(int64_t n_tiles) {
+    return (int64_t)blockIdx.x < n_tiles ? (int)blockIdx.x : -1;
+}
+
 template <int RPH, bool INNER>
 __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
     constexpr int N = 2 * RPH;
@@ -179,13 +191,28 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // CTA g's first tile is tile g; the tensor is never written, so its first chunks can
+    // be in flight while the kernel before this one finishes (the packed factor chunks,
+    // which that kernel writes, follow after the wait)
+    const int first_tile = g_first_tile(P.n_tiles);
+    const int npre = first_tile >= 0 ? (P.n_kc < kTcStages ? P.n_kc : kTcStages) : 0;
+    if (warp == 4 && lane == 0) {
+        prefetch_tensormap(&tmap);
+        if (first_tile >= 0) {
+            int64_t ib, ot;
+            tile_coords<INNER>(P, first_tile, ib, ot);
+            for (int kc = 0; kc < npre; ++kc) {
+                mbar_arrive_expect_tx(&full[kc], (uint32_t)kStage);
+                tma_load_3d(base_ptr + kc * kStage, &tmap, &full[kc], kc * 64, (int)(ib * P.I_T), (int)(ot * P.O_T));
+            }
+        }
+    }
     pdl_wait();
     pdl_trigger();
 
     if (warp == 4) {
         // ------------------------- scheduler + producer -------------------------
         if (lane == 0) {
-            prefetch_tensormap(&tmap);
             int stage = 0;
             uint32_t phase = 0;
             int64_t issued = 0;
@@ -195,25 +222,33 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
                     record_device_error(P.err, kErrWaitEmpty);
                     break;
                 }
-                const unsigned int grab = atomicAdd(P.sched, 1u);
-                const int t = grab < (unsigned int)P.n_tiles ? (int)grab : -1;
+                int t = first_tile;
+                if (s > 0) {
+                    // tiles G, G+1, ... go to whichever CTA asks first
+                    const unsigned int grab = atomicAdd(P.sched, 1u) + (unsigned int)gridDim.x;
+                    t = grab < (unsigned int)P.n_tiles ? (int)grab : -1;
+                }
                 tile_ring[slot] = t;
                 mbar_arrive(&sfull[slot]);              // releases the slot to the consumers
                 if (t < 0) break;
                 int64_t ib, ot;
-                if (INNER) { ib = t / P.n_ot; ot = t % P.n_ot; }
-                else { ot = t / P.nb; ib = t % P.nb; }
+                tile_coords<INNER>(P, t, ib, ot);
                 bool ok = true;
                 for (int kc = 0; kc < P.n_kc; ++kc) {
-                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
-                        record_device_error(P.err, kErrWaitEmpty);
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_expect_tx(&full[stage], (uint32_t)kStage);
                     unsigned char* st = base_ptr + stage * kStage;
-                    tma_load_3d(st, &tmap, &full[stage], kc * 64, (int)(ib * P.I_T), (int)(ot * P.O_T));
-                    bulk_load(st + kBoxBytes, P.FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
+                    if (s == 0 && kc < npre) {
+                        // stage kc already holds (or is receiving) this chunk of the tensor
+                        bulk_load(st + kBoxBytes, P.FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
+                    } else {
+                        if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
+                            record_device_error(P.err, kErrWaitEmpty);
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full[stage], (uint32_t)kStage);
+                        tma_load_3d(st, &tmap, &full[stage], kc * 64, (int)(ib * P.I_T), (int)(ot * P.O_T));
+                        bulk_load(st + kBoxBytes, P.FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
+                    }
                     ++issued;
                     if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
                 }
@@ -289,8 +324,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
         if (lane == 0) mbar_arrive(&sempty[slot]);
         if (t < 0) break;
         int64_t ib, ot;
-        if (INNER) { ib = t / P.n_ot; ot = t % P.n_ot; }
-        else { ot = t / P.nb; ib = t % P.nb; }
+        tile_coords<INNER>(P, t, ib, ot);
         // weights of this row, fetched while the tile is being contracted
         float w[RPH];
         bool row_live;

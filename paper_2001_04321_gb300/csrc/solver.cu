@@ -428,6 +428,7 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
 }
 
 constexpr int kMaxGraphIters = 1024;
+constexpr int kGraphChunk = 32;
 
 // Capture `iters` outer iterations into one executable graph.
 static ntf_status capture_graph(Solver* S, int iters, cudaStream_t st) {
@@ -470,17 +471,36 @@ static ntf_status run_solver(Solver* S, int iters, cudaStream_t st) {
     }
     if (S->timing && iters > kMaxGraphIters)
         return fail(NTF_EINVAL, "timed graph runs are limited to 1024 iterations per call");
-    int left = iters;
-    while (left > 0) {
-        const int chunk = left < kMaxGraphIters ? left : kMaxGraphIters;
-        if (!S->gexec || S->gstream != st || S->g_iters != chunk || S->g_timing != S->timing_every) {
-            ntf_status s = capture_graph(S, chunk, st);
+    const bool have = S->gexec && S->gstream == st && S->g_timing == S->timing_every;
+    if (S->timing || (have && S->g_iters == iters)) {
+        // timed runs (and a run matching a prepared graph) replay one graph of all iterations,
+        // so that every timed launch belongs to the replay the events are read from
+        if (!have || S->g_iters != iters) {
+            ntf_status s = capture_graph(S, iters, st);
             if (s != NTF_OK) return s;
         }
         NTF_CUDA_TRY(cudaGraphLaunch(S->gexec, st));
         count_launch((int)S->g_kernels);
-        left -= chunk;
-        S->iters_done += chunk;
+        S->iters_done += iters;
+        return NTF_OK;
+    }
+    // otherwise a graph of kGraphChunk iterations is captured once and replayed; the
+    // remainder runs eagerly (instantiation time grows with the graph, replay does not)
+    int left = iters;
+    while (left >= kGraphChunk) {
+        if (!S->gexec || S->gstream != st || S->g_iters != kGraphChunk || S->g_timing != S->timing_every) {
+            ntf_status s = capture_graph(S, kGraphChunk, st);
+            if (s != NTF_OK) return s;
+        }
+        NTF_CUDA_TRY(cudaGraphLaunch(S->gexec, st));
+        count_launch((int)S->g_kernels);
+        left -= kGraphChunk;
+        S->iters_done += kGraphChunk;
+    }
+    for (; left > 0; --left) {
+        ntf_status s = S->iterate(st);
+        if (s != NTF_OK) return s;
+        ++S->iters_done;
     }
     return NTF_OK;
 }
