@@ -121,6 +121,14 @@ NTF_API const char* ntf_last_error(void);
  * NTF_ETIMEOUT (a kernel gave up a bounded wait) or NTF_ECUDA. */
 NTF_API ntf_status ntf_device_status(void* stream);
 
+/* Check of the failure path (no paper counterpart): launches one kernel whose
+ * single thread waits on an mbarrier that nothing arrives on, gives up after
+ * `limit_ns` nanoseconds (1e3..2e9) as every bounded wait of this library does,
+ * records the time-out in the device error word and returns.  The call then
+ * synchronises `stream` and returns ntf_device_status(): NTF_ETIMEOUT when the
+ * path works (the word is cleared and the context stays usable). */
+NTF_API ntf_status ntf_check_wait_timeout(int64_t limit_ns, void* stream);
+
 /* Number of kernels this library has launched in this process. */
 NTF_API int64_t ntf_launch_count(void);
 

@@ -85,6 +85,7 @@ _SIGS = {
                                  _P]),
     "ntf_her_extrapolate": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P]),
     "ntf_block_gradient": (C.c_int, [_P, C.c_int64, C.c_int, _P, _P, _P, C.c_double, _P, _P]),
+    "ntf_check_wait_timeout": (C.c_int, [C.c_int64, _P]),
     "ntf_objective": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int, _P, _P, _P]),
     "ntf_residual_workspace_bytes": (C.c_size_t, [C.POINTER(_Tensor), C.c_int]),
     "ntf_residual_sq": (C.c_int, [C.POINTER(_Tensor), C.POINTER(_P), C.c_int, _P, _P, C.c_size_t, _P]),
@@ -191,6 +192,11 @@ def _ptr_array(ts) -> "C.Array":
     for i, t in enumerate(ts):
         arr[i] = None if t is None else t.data_ptr()
     return arr
+
+
+def check_wait_timeout(limit_ns: int = 10_000_000, stream=None) -> int:
+    """Run the bounded-wait self-check; returns the status (NTF_ETIMEOUT when the path works)."""
+    return int(load().ntf_check_wait_timeout(int(limit_ns), _stream(stream)))
 
 
 def launch_count() -> int:

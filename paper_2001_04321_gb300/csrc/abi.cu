@@ -87,6 +87,15 @@ ntf_status ntf_device_status(void* stream) {
     return NTF_OK;
 }
 
+ntf_status ntf_check_wait_timeout(int64_t limit_ns, void* stream) {
+    if (limit_ns < 1000 || limit_ns > 2000000000ll) return fail(NTF_EINVAL, "limit_ns must be in [1e3, 2e9]");
+    int* w = device_error_word();
+    if (!w) return fail(NTF_ECUDA, "device error word unavailable");
+    cudaError_t e = launch_wait_check(limit_ns, w, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "ntf_check_wait_timeout");
+    return ntf_device_status(stream);
+}
+
 void ntf_opts_default(ntf_opts* o) {
     if (!o) return;
     o->her = 1;

@@ -463,28 +463,48 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // the first tiles of this CTA's range: the tensor is never written, so their boxes
+    // can be in flight while the kernel before this one finishes (the packed A_{N-2}
+    // blocks, which that kernel writes, follow after the wait)
+    const int64_t left = P.C - (int64_t)cb * 128;
+    const int nbox = left > 64 ? 2 : 1;
+    const int npre = (int)(t_end - t_beg < kTcStages ? t_end - t_beg : kTcStages);
+    if (warp == 4 && lane == 0) {
+        prefetch_tensormap(&tmap);
+        for (int q = 0; q < npre; ++q) {
+            const int64_t t = t_beg + q;
+            const int64_t ib = t / P.n_ot, o = t % P.n_ot;   // I_T = 128, O_T = 1
+            mbar_arrive_expect_tx(&full[q], (uint32_t)(nbox * kBoxBytes + kB));
+            for (int b = 0; b < nbox; ++b)
+                tma_load_3d(base_ptr + q * kStage + b * kBoxBytes, &tmap, &full[q], cb * 128 + b * 64, (int)(ib * 128),
+                            (int)o);
+        }
+    }
     pdl_wait();
     pdl_trigger();
 
     if (warp == 4) {
         if (lane == 0) {
-            prefetch_tensormap(&tmap);
             int stage = 0;
             uint32_t phase = 0;
             int64_t issued = 0;
-            const int64_t left = P.C - (int64_t)cb * 128;
-            const int nbox = left > 64 ? 2 : 1;
             for (int64_t t = t_beg; t < t_end; ++t) {
                 const int64_t ib = t / P.n_ot, o = t % P.n_ot;   // I_T = 128, O_T = 1
-                if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
-                    record_device_error(P.err, kErrWaitEmpty);
-                    break;
-                }
-                mbar_arrive_expect_tx(&full[stage], (uint32_t)(nbox * kBoxBytes + kB));
                 unsigned char* st = base_ptr + stage * kStage;
-                for (int b = 0; b < nbox; ++b)
-                    tma_load_3d(st + b * kBoxBytes, &tmap, &full[stage], cb * 128 + b * 64, (int)(ib * 128), (int)o);
-                bulk_load(st + kT, P.FcT + ib * kB, (uint32_t)kB, &full[stage]);
+                if (issued < npre) {
+                    // stage `issued` already receives this tile's boxes
+                    bulk_load(st + kT, P.FcT + ib * kB, (uint32_t)kB, &full[stage]);
+                } else {
+                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
+                        record_device_error(P.err, kErrWaitEmpty);
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[stage], (uint32_t)(nbox * kBoxBytes + kB));
+                    for (int b = 0; b < nbox; ++b)
+                        tma_load_3d(st + b * kBoxBytes, &tmap, &full[stage], cb * 128 + b * 64, (int)(ib * 128),
+                                    (int)o);
+                    bulk_load(st + kT, P.FcT + ib * kB, (uint32_t)kB, &full[stage]);
+                }
                 ++issued;
                 if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
             }

@@ -393,6 +393,31 @@ cudaError_t launch_block_gradient(const float* A, int64_t rows, int r, const flo
 }
 
 // ---------------------------------------------------------------------------
+// check of the bounded-wait path: one thread waits on an mbarrier that nothing
+// arrives on, gives up after limit_ns, records the time-out code and returns
+// ---------------------------------------------------------------------------
+__global__ void k_wait_check(int64_t limit_ns, int* err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        if (mbar_try_wait(&bar, 0)) return;                 // cannot happen: nothing arrives
+        if (global_timer_ns() - t0 > (uint64_t)limit_ns) {
+            record_device_error(err, kErrWaitFull);
+            return;
+        }
+    }
+}
+
+cudaError_t launch_wait_check(int64_t limit_ns, int* err, cudaStream_t st) {
+    k_wait_check<<<1, 32, 0, st>>>(limit_ns, err);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // a4: extrapolation  A_hat = max(0, A + beta (A - A_prev))
 // ---------------------------------------------------------------------------
 __global__ void k_extrapolate(const float* __restrict__ A, const float* __restrict__ Ap,

@@ -29,6 +29,7 @@ size_t bcd_workspace(int64_t rows);
 cudaError_t launch_bcd(int method, float* A, int64_t rows, int r, const float* M, const double* V, int inner_max,
                        double tol, void* ws, cudaStream_t st);
 
+cudaError_t launch_wait_check(int64_t limit_ns, int* err, cudaStream_t st);
 cudaError_t launch_block_gradient(const float* A, int64_t rows, int r, const float* M, const double* V,
                                   const double* scale_dev, double scale, float* out, cudaStream_t st);
 cudaError_t launch_extrapolate(const float* A, const float* Ap, const double* beta, int64_t n, float* Ah,

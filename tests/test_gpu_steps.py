@@ -190,3 +190,16 @@ def test_her_step_golden_table_and_copies():
         Ah[1].add_(0.25)
     s = ntf.her_state_read(state)
     assert s["iters"] == 6 and s["restarts"] == 3
+
+
+def test_bounded_wait_gives_up_and_reports_timeout():
+    # a kernel waits on an mbarrier that nothing arrives on: it gives up after 10 ms,
+    # the host reads NTF_ETIMEOUT, the error word is cleared and the context stays usable
+    import torch
+    import paper_2001_04321_gb300 as ntf
+    st = ntf.check_wait_timeout(10_000_000)
+    assert st == 5   # NTF_ETIMEOUT
+    ntf.device_status()   # cleared: no error now
+    A = torch.rand(100, 8, device="cuda")
+    G = ntf.gram(A).cpu().numpy()
+    assert np.allclose(G, (A.double().T @ A.double()).cpu().numpy(), rtol=1e-6)
