@@ -234,15 +234,25 @@ __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) 
     const int cn = __ldcg(P.B.cur + n);
     float* A = P.B.X[n][cn];                      // in: A_{k-1}, out: A_k
     float* Ah = her ? P.B.X[n][1 - cn] : nullptr; // out: A_hat_k
-    for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
-        const int l = q >> 5, c = q & 31;
-        Vs[l * 33 + c] = (l < r && c < r) ? __ldcg(P.Vf + l * r + c) : 0.f;
+    if (!P.v_from_stream) {
+        for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+            const int l = q >> 5, c = q & 31;
+            Vs[l * 33 + c] = (l < r && c < r) ? __ldcg(P.Vf + l * r + c) : 0.f;
+        }
     }
     const float beta = her ? (float)__ldcg(P.beta) : 0.f;
     const float a_old = (live && piece == 0) ? __ldcg(A + row * r + lane) : 0.f;
     pdl_wait();
     pdl_trigger();
+    if (P.v_from_stream) {
+        // V was formed by the stream this kernel follows: read it only after the wait
+        for (int q = threadIdx.x; q < 32 * 32; q += blockDim.x) {
+            const int l = q >> 5, c = q & 31;
+            Vs[l * 33 + c] = (l < r && c < r) ? __ldcg(P.Vf + l * r + c) : 0.f;
+        }
+    }
 
+    if (P.sched_next && blockIdx.x == 0 && threadIdx.x == 0) *P.sched_next = 0u;
     // M row pieces from the stream's partial sums
     float m = live ? reduce_piece(P.red, row, lane, piece, kEpiPieces) : 0.f;
     if (piece > 0) mpiece[piece - 1][rw][lane] = m;
@@ -282,6 +292,19 @@ __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) 
                 Ah[row * r + lane] = ah;
             }
             inner = m * a;
+            // the next stream's tensor-core operand: bf16 hi | lo of this row
+            __nv_bfloat16* pa = P.packA[cn];
+            __nv_bfloat16* ph = her ? P.packH[1 - cn] : nullptr;
+            if (pa) {
+                const __nv_bfloat16 hi = __float2bfloat16_rn(a);
+                pa[packed_index(row, lane, P.pack_rph)] = hi;
+                pa[packed_index(row, P.pack_rph + lane, P.pack_rph)] = __float2bfloat16_rn(a - __bfloat162float(hi));
+            }
+            if (ph) {
+                const __nv_bfloat16 hi = __float2bfloat16_rn(ah);
+                ph[packed_index(row, lane, P.pack_rph)] = hi;
+                ph[packed_index(row, P.pack_rph + lane, P.pack_rph)] = __float2bfloat16_rn(ah - __bfloat162float(hi));
+            }
         }
         rowsA[rw][lane] = live ? a : 0.f;
         rowsH[rw][lane] = live ? ah : 0.f;

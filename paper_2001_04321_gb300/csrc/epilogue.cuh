@@ -1,7 +1,9 @@
 // Fused prep / epilogue / finish kernels of the solver's main path (see epilogue.cu).
 #pragma once
 
+#include "fused.cuh"
 #include "mttkrp.cuh"
+#include "mttkrp_tc.cuh"
 #include "small.cuh"
 
 namespace ntf {
@@ -61,6 +63,12 @@ struct EpiParams {
     double* fhat_out;
     int* iters_out;        // outer-iteration counter
     ntf_her_state* her;    // nullptr without HER
+    // fused 3-way tensor-core path: the operands of the next stream written here
+    __nv_bfloat16* packA[2];   // A_k's rows go to packA[cur] (if set), in the tensor-core layout
+    __nv_bfloat16* packH[2];   // A_hat_k's rows go to packH[1 - cur] (if set)
+    int pack_rph;
+    unsigned int* sched_next;  // run-time tile counter of the next stream, set to 0 here (or nullptr)
+    int v_from_stream;         // V is formed by the preceding stream (read after the wait)
 };
 
 cudaError_t launch_prep(const PrepParams& P, cudaStream_t st, bool pdl);
@@ -68,7 +76,9 @@ cudaError_t launch_epilogue(const EpiParams& P, cudaStream_t st, bool pdl);
 int epilogue_blocks(int64_t rows);
 
 // streaming kernel of a plan alone (the packed factors / W already in place)
+// `fused` (tensor-core plans only): device-chosen operands and the Gram job (see TcParams)
 ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* workspace, cudaStream_t st,
-                             TmapCache* cache, StreamTimer* timer, bool pdl = false);
+                             TmapCache* cache, StreamTimer* timer, bool pdl = false,
+                             const TcParams* fused = nullptr);
 
 }  // namespace ntf

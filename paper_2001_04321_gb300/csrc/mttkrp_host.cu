@@ -345,7 +345,7 @@ static ntf_status get_tensor_map(const TensorView& v, const MttkrpPlan& P, TmapC
 }
 
 ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* workspace, cudaStream_t st,
-                             TmapCache* cache, StreamTimer* timer, bool pdl) {
+                             TmapCache* cache, StreamTimer* timer, bool pdl, const TcParams* fused) {
     unsigned char* ws = static_cast<unsigned char*>(workspace);
     CUtensorMap local_map;
     const CUtensorMap* map = nullptr;
@@ -392,8 +392,25 @@ ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* wor
         T.FcT = ws + P.off_Fc;
         T.Fi = S.Fi;
         T.W = S.W;
+        T.ldw = P.RP;
         T.part = S.part;
         T.err = S.err;
+        if (fused) {
+            // operands chosen on the device, and the Gram job for the following epilogue
+            T.ldw = fused->ldw;
+            T.cur = fused->cur;
+            for (int k = 0; k < 2; ++k) {
+                T.FcTb[k] = fused->FcTb[k];
+                T.Fib[k] = fused->Fib[k];
+                T.Wb[k] = fused->Wb[k];
+            }
+            T.fct_sel = fused->fct_sel;
+            T.fi_sel = fused->fi_sel;
+            T.fi_flip = fused->fi_flip;
+            T.w_sel = fused->w_sel;
+            T.w_flip = fused->w_flip;
+            T.job = fused->job;
+        }
         grid = P.kind == ModeKind::Last ? dim3(P.G, P.n_cb, 1) : dim3(P.G, 1, 1);
         smem = P.kind == ModeKind::Last ? tc_last_smem(P.RPH) : tc_rows_smem(P.RPH);
         if (timer && timer->start) NTF_CUDA_TRY(record_timer_event(timer->start, st));

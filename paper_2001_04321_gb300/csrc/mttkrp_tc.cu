@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
     if (warp == 4) {
         // ------------------------- scheduler + producer -------------------------
         if (lane == 0) {
+            const unsigned char* FcT = P.cur ? P.FcTb[__ldcg(P.cur + P.fct_sel)] : P.FcT;
             int stage = 0;
             uint32_t phase = 0;
             int64_t issued = 0;
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
                     unsigned char* st = base_ptr + stage * kStage;
                     if (s == 0 && kc < npre) {
                         // stage kc already holds (or is receiving) this chunk of the tensor
-                        bulk_load(st + kBoxBytes, P.FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
+                        bulk_load(st + kBoxBytes, FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
                     } else {
                         if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
                             record_device_error(P.err, kErrWaitEmpty);
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
                         }
                         mbar_arrive_expect_tx(&full[stage], (uint32_t)kStage);
                         tma_load_3d(st, &tmap, &full[stage], kc * 64, (int)(ib * P.I_T), (int)(ot * P.O_T));
-                        bulk_load(st + kBoxBytes, P.FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
+                        bulk_load(st + kBoxBytes, FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
                     }
                     ++issued;
                     if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
@@ -308,6 +309,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
     }
 
     // ------------------------------ epilogue (warps 0-3) ------------------------------
+    // before the first accumulator is ready: this CTA's share of the Grams and V for the
+    // epilogue that follows the stream
+    gram_job_run(P.job, (int)blockIdx.x * 4 + warp, (int)gridDim.x * 4);
+    const float* Wt = P.cur ? P.Wb[__ldcg(P.cur + P.w_sel) ^ P.w_flip] : P.W;
+    const float* Fit = P.cur ? P.Fib[__ldcg(P.cur + P.fi_sel) ^ P.fi_flip] : P.Fi;
     const int m = threadIdx.x;                       // tile row = TMEM lane
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
@@ -331,15 +337,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
         if (INNER) {
             const int64_t o = ot * P.O_T + m / P.I_T;
             row_live = o < P.n_o && ib * P.I_T + m % P.I_T < P.Ii;
-            const float* src = P.W + (row_live ? o : 0) * P.RP;
+            const float* src = Wt + (row_live ? o : 0) * P.ldw;
 #pragma unroll
-            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.RP) ? __ldg(src + p) : 0.f;
+            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(src + p) : 0.f;
         } else {
             const int64_t i = ib * 128 + m;
             row_live = i < P.Ii;
-            const float* src = P.Fi + (row_live ? i : 0) * P.RP;
+            const float* src = Fit + (row_live ? i : 0) * P.ldw;
 #pragma unroll
-            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.RP) ? __ldg(src + p) : 0.f;
+            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(src + p) : 0.f;
         }
         // Y(row) = sum over the tile's 64-column chunks of the chunk accumulators (IEEE FP32 adds)
         float y[RPH];
@@ -485,6 +491,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
 
     if (warp == 4) {
         if (lane == 0) {
+            const unsigned char* FcT = P.cur ? P.FcTb[__ldcg(P.cur + P.fct_sel)] : P.FcT;
             int stage = 0;
             uint32_t phase = 0;
             int64_t issued = 0;
@@ -493,7 +500,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
                 unsigned char* st = base_ptr + stage * kStage;
                 if (issued < npre) {
                     // stage `issued` already receives this tile's boxes
-                    bulk_load(st + kT, P.FcT + ib * kB, (uint32_t)kB, &full[stage]);
+                    bulk_load(st + kT, FcT + ib * kB, (uint32_t)kB, &full[stage]);
                 } else {
                     if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
                         record_device_error(P.err, kErrWaitEmpty);
@@ -503,7 +510,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
                     for (int b = 0; b < nbox; ++b)
                         tma_load_3d(st + b * kBoxBytes, &tmap, &full[stage], cb * 128 + b * 64, (int)(ib * 128),
                                     (int)o);
-                    bulk_load(st + kT, P.FcT + ib * kB, (uint32_t)kB, &full[stage]);
+                    bulk_load(st + kT, FcT + ib * kB, (uint32_t)kB, &full[stage]);
                 }
                 ++issued;
                 if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
@@ -552,6 +559,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
     }
 
     // ---------------- warps 0-3: fold W(o,:) x tile accumulator into registers ----------------
+    // first, this CTA's share of the Grams and V for the epilogue that follows the stream
+    gram_job_run(P.job, ((int)blockIdx.y * (int)gridDim.x + (int)blockIdx.x) * 4 + warp,
+                 (int)(gridDim.x * gridDim.y) * 4);
+    const float* Wt = P.cur ? P.Wb[__ldcg(P.cur + P.w_sel) ^ P.w_flip] : P.W;
     const int m = threadIdx.x;
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
@@ -562,9 +573,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
     for (int64_t t = t_beg; t < t_end; ++t, ++tl) {
         const int64_t o = t % P.n_ot;
         float w[RPH];
-        const float* wr = P.W + o * P.RP;
+        const float* wr = Wt + o * P.ldw;
 #pragma unroll
-        for (int p = 0; p < RPH; ++p) w[p] = p < P.RP ? __ldg(wr + p) : 0.f;
+        for (int p = 0; p < RPH; ++p) w[p] = p < P.r ? __ldg(wr + p) : 0.f;
         const int d = (int)(tl % kLastDbuf);
         if (ok && !warp_wait(&tfull[d], (uint32_t)((tl / kLastDbuf) & 1))) {
             if (lane == 0) record_device_error(P.err, kErrWaitFull);

@@ -1,6 +1,8 @@
 // tcgen05 MTTKRP kernels for bf16 tensor storage (see mttkrp_tc.cu).
 #pragma once
 
+#include "fused.cuh"
+
 #include "ntf_common.cuh"
 
 namespace ntf {
@@ -15,11 +17,20 @@ struct TcParams {
     int64_t Cpad;
     const unsigned char* FcT;   // rows kernel: A_{N-1} per 64-row chunk; last kernel: A_{N-2} per 128-row
                                 // block; N rows x 128 B per 64 rows, swizzled bf16 hi|lo
-    const float* Fi;            // packed A_{N-2}: Ii x RP (fp32)
-    const float* W;             // n_o x RP (fp32)
+    const float* Fi;            // A_{N-2} rows (fp32), row stride ldw
+    const float* W;             // n_o weight rows (fp32), row stride ldw
+    int ldw;                    // RP for packed tables, r when W / Fi are factor rows
     float* part;                // rows kernels: one slot per tile; last kernel: one per CTA
     unsigned int* sched;        // rows kernels: next tile to hand out (0 before every launch)
     int* err;
+    // fused solver path: operands chosen on the device from the current-buffer indices
+    // (cur == nullptr: FcT, Fi and W are used as given)
+    const int* cur;
+    const unsigned char* FcTb[2];   // FcT = FcTb[cur[fct_sel]]
+    const float* Fib[2];            // Fi = Fib[cur[fi_sel] ^ fi_flip]
+    const float* Wb[2];             // W = Wb[cur[w_sel] ^ w_flip]
+    int fct_sel, fi_sel, fi_flip, w_sel, w_flip;
+    GramJob job;                    // Grams + V for the epilogue after this stream (job.rr == 0: none)
 };
 
 size_t tc_rows_smem(int rph);

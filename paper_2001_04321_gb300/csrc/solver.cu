@@ -61,6 +61,12 @@ struct Solver {
     float* gpart = nullptr;
     double* ipart = nullptr;
     double* qpart = nullptr;
+    unsigned char* wsm[NTF_MAX_ORDER] = {nullptr};   // each mode's MTTKRP workspace (inside ws_mt)
+    // 3-way tensor-core path without k_prep
+    bool direct = false;
+    bool prepped = false;
+    __nv_bfloat16* packRows[2] = {nullptr, nullptr};   // packed A_{N-1} of buffer k (row streams)
+    __nv_bfloat16* packLast = nullptr;                 // packed pairing A_{N-2} (last-mode stream)
     // graph replay: one graph holds g_iters outer iterations (and, when timing is
     // on, the event records around each MTTKRP stream, read after the replay)
     cudaGraphExec_t gexec = nullptr;
@@ -131,76 +137,174 @@ struct Solver {
         return B;
     }
 
-    // one outer iteration on the fused path: per mode prep -> stream -> epilogue;
+    // preparation of mode n's stream: V_n, the finished Grams of the mode before, and
+    // the packed operands in mode n's workspace
+    PrepParams make_prep(int n) const {
+        const bool use_her = o.her != 0;
+        unsigned char* ws = wsm[n];
+        const MttkrpPlan& P = plan[n];
+        PrepParams pp{};
+        pp.B = fused_bufs();
+        pp.order = N;
+        pp.mode = n;
+        pp.skip = P.kind == ModeKind::Outer ? n : -1;
+        pp.r = r;
+        pp.RP = P.RP;
+        pp.C = vs.C;
+        pp.Ii = vs.Ii;
+        pp.n_o = vs.n_o;
+        pp.Fc_rows_out = round_up(vs.C, 64);
+        for (int l = 0; l < N; ++l) pp.dims[l] = vs.dims[l];
+        pp.V = V;
+        pp.Vf = Vf;
+        pp.Fc = (P.kind != ModeKind::Last && !P.tc) ? reinterpret_cast<float*>(ws + P.off_Fc) : nullptr;
+        pp.FcT = P.tc ? reinterpret_cast<__nv_bfloat16*>(ws + P.off_Fc) : nullptr;
+        pp.RPH = P.RPH;
+        if (P.kind == ModeKind::Last) {      // tensor-core last mode: A_{N-2}, two chunks per 128-row block
+            pp.fct_mode = N - 2;
+            pp.fct_rows = vs.Ii;
+            pp.n_kc = (int)(2 * P.nb);
+        } else {
+            pp.fct_mode = N - 1;
+            pp.fct_rows = vs.C;
+            pp.n_kc = P.n_kc;
+        }
+        pp.Fi = (P.kind != ModeKind::Inner && !(P.tc && P.kind == ModeKind::Last))
+                    ? reinterpret_cast<float*>(ws + P.off_Fi)
+                    : nullptr;
+        pp.W = reinterpret_cast<float*>(ws + P.off_W);
+        pp.sched = P.tile_slots ? reinterpret_cast<unsigned int*>(ws + P.off_sched) : nullptr;
+        pp.fin_mode = n > 0 ? n - 1 : N - 1;
+        pp.fin_blocks = epilogue_blocks(vs.dims[pp.fin_mode]);
+        pp.gpart = gpart;
+        pp.her = use_her ? her : nullptr;
+        return pp;
+    }
+
+    EpiParams make_epi(int n) const {
+        const bool use_her = o.her != 0;
+        unsigned char* ws = wsm[n];
+        const MttkrpPlan& P = plan[n];
+        EpiParams ep{};
+        ep.B = fused_bufs();
+        ep.red = make_reduce_params(vs, P, reinterpret_cast<const float*>(ws + P.off_part),
+                                    reinterpret_cast<const float*>(ws + P.off_W));
+        ep.mode = n;
+        ep.order = N;
+        ep.rows = vs.dims[n];
+        ep.r = r;
+        ep.last = n == N - 1 ? 1 : 0;
+        ep.beta = &her->beta;
+        ep.V = V;
+        ep.Vf = Vf;
+        ep.gpart = gpart;
+        ep.ipart = ipart;
+        ep.qpart = qpart;
+        ep.ticket = iters_dev + 1;
+        ep.tnorm = &scal[0];
+        ep.fhat_out = &scal[1];
+        ep.iters_out = iters_dev;
+        ep.her = use_her ? her : nullptr;
+        return ep;
+    }
+
+    // The 3-way tensor-core path runs without k_prep: the stream kernels read W and
+    // A_{N-2} straight from the factor buffers (chosen on the device from cur[]), take
+    // their packed operand from buffers the epilogues write, and finish the Grams and V
+    // for the epilogue that follows them in their idle epilogue warps.  k_prep runs once,
+    // before the first stream.
+    ntf_status ensure_prepped(cudaStream_t st) {
+        if (!direct || prepped) return NTF_OK;
+        PrepParams pp = make_prep(0);
+        pp.FcT = packRows[0];            // cur is 0 before the first decision
+        pp.fin_mode = -1;
+        cudaError_t e = launch_prep(pp, st, false);
+        if (e != cudaSuccess) return cuda_fail(e, "prep");
+        prepped = true;
+        return NTF_OK;
+    }
+
+    TcParams direct_stream(int n) const {
+        const bool use_her = o.her != 0;
+        TcParams T{};
+        T.ldw = r;
+        T.cur = cur;
+        if (n < N - 1) {
+            T.FcTb[0] = reinterpret_cast<const unsigned char*>(packRows[0]);
+            T.FcTb[1] = reinterpret_cast<const unsigned char*>(packRows[1]);
+            T.fct_sel = N - 1;
+        } else {
+            T.FcTb[0] = T.FcTb[1] = reinterpret_cast<const unsigned char*>(packLast);
+            T.fct_sel = 0;
+        }
+        // 3-way: the outer mode's row weights are A_1 (not yet updated), the inner and last
+        // modes' W is A_0's pairing factor (A_hat_0 with HER)
+        T.Fib[0] = X[1][0];
+        T.Fib[1] = X[1][1];
+        T.fi_sel = 1;
+        T.fi_flip = 0;
+        T.Wb[0] = X[0][0];
+        T.Wb[1] = X[0][1];
+        T.w_sel = 0;
+        T.w_flip = (use_her && n > 0) ? 1 : 0;
+        GramJob& J = T.job;
+        J.rr = r * r;
+        J.order = N;
+        J.mode = n;
+        J.fin_mode = n > 0 ? n - 1 : N - 1;
+        J.fin_blocks = epilogue_blocks(vs.dims[J.fin_mode]);
+        J.her = use_her ? 1 : 0;
+        J.gpart = gpart;
+        for (int l = 0; l < N; ++l)
+            for (int k = 0; k < 2; ++k) J.GB[l][k] = GB[l][k];
+        J.V = V;
+        J.Vf = Vf;
+        J.cur = cur;
+        J.iters = iters_dev;
+        J.hs = use_her ? her : nullptr;
+        return T;
+    }
+
+    // one outer iteration on the fused path: per mode (prep ->) stream -> epilogue;
     // the last epilogue also takes F_hat, the decision and the buffer flip
     ntf_status iterate_fused(cudaStream_t st) {
+        if (direct && !prepped) return fail(NTF_EINVAL, "internal: fused iteration before its first preparation");
         const bool use_her = o.her != 0;
-        unsigned char* ws = static_cast<unsigned char*>(ws_mt);
-        const FusedBufs fb = fused_bufs();
         for (int n = 0; n < N; ++n) {
             const MttkrpPlan& P = plan[n];
-            PrepParams pp{};
-            pp.B = fb;
-            pp.order = N;
-            pp.mode = n;
-            pp.skip = P.kind == ModeKind::Outer ? n : -1;
-            pp.r = r;
-            pp.RP = P.RP;
-            pp.C = vs.C;
-            pp.Ii = vs.Ii;
-            pp.n_o = vs.n_o;
-            pp.Fc_rows_out = round_up(vs.C, 64);
-            for (int l = 0; l < N; ++l) pp.dims[l] = vs.dims[l];
-            pp.V = V;
-            pp.Vf = Vf;
-            pp.Fc = (P.kind != ModeKind::Last && !P.tc) ? reinterpret_cast<float*>(ws + P.off_Fc) : nullptr;
-            pp.FcT = P.tc ? reinterpret_cast<__nv_bfloat16*>(ws + P.off_Fc) : nullptr;
-            pp.RPH = P.RPH;
-            if (P.kind == ModeKind::Last) {      // tensor-core last mode: A_{N-2}, two chunks per 128-row block
-                pp.fct_mode = N - 2;
-                pp.fct_rows = vs.Ii;
-                pp.n_kc = (int)(2 * P.nb);
-            } else {
-                pp.fct_mode = N - 1;
-                pp.fct_rows = vs.C;
-                pp.n_kc = P.n_kc;
+            if (!direct) {
+                cudaError_t e = launch_prep(make_prep(n), st, pdl);
+                if (e != cudaSuccess) return cuda_fail(e, "prep");
             }
-            pp.Fi = (P.kind != ModeKind::Inner && !(P.tc && P.kind == ModeKind::Last))
-                        ? reinterpret_cast<float*>(ws + P.off_Fi)
-                        : nullptr;
-            pp.W = reinterpret_cast<float*>(ws + P.off_W);
-            pp.sched = P.tile_slots ? reinterpret_cast<unsigned int*>(ws + P.off_sched) : nullptr;
-            pp.fin_mode = n > 0 ? n - 1 : N - 1;
-            pp.fin_blocks = epilogue_blocks(vs.dims[pp.fin_mode]);
-            pp.gpart = gpart;
-            pp.her = use_her ? her : nullptr;
-            cudaError_t e = launch_prep(pp, st, pdl);
-            if (e != cudaSuccess) return cuda_fail(e, "prep");
             // a kernel right after an event record is launched without the PDL attribute
             StreamTimer* timer = next_timer();
-            ntf_status s = run_mttkrp_stream(vs, P, ws_mt, st, &tm[n], timer, pdl);
+            ntf_status s;
+            if (direct) {
+                const TcParams T = direct_stream(n);
+                s = run_mttkrp_stream(vs, P, wsm[n], st, &tm[n], timer, pdl, &T);
+            } else {
+                s = run_mttkrp_stream(vs, P, wsm[n], st, &tm[n], timer, pdl);
+            }
             if (s != NTF_OK) return s;
-            EpiParams ep{};
-            ep.B = fb;
-            ep.red = make_reduce_params(vs, P, reinterpret_cast<const float*>(ws + P.off_part),
-                                        reinterpret_cast<const float*>(ws + P.off_W));
-            ep.mode = n;
-            ep.order = N;
-            ep.rows = vs.dims[n];
-            ep.r = r;
-            ep.last = n == N - 1 ? 1 : 0;
-            ep.beta = &her->beta;
-            ep.V = V;
-            ep.Vf = Vf;
-            ep.gpart = gpart;
-            ep.ipart = ipart;
-            ep.qpart = qpart;
-            ep.ticket = iters_dev + 1;
-            ep.tnorm = &scal[0];
-            ep.fhat_out = &scal[1];
-            ep.iters_out = iters_dev;
-            ep.her = use_her ? her : nullptr;
-            e = launch_epilogue(ep, st, pdl && !timer);
+            EpiParams ep = make_epi(n);
+            if (direct) {
+                const int nx = (n + 1) % N;
+                const MttkrpPlan& Q = plan[nx];
+                ep.sched_next = Q.tile_slots ? reinterpret_cast<unsigned int*>(wsm[nx] + Q.off_sched) : nullptr;
+                ep.v_from_stream = 1;
+                if (n == N - 1) {
+                    // the next iteration's row streams read A_{N-1} (or A_hat_{N-1} after an accept)
+                    ep.packA[0] = ep.packH[0] = packRows[0];
+                    ep.packA[1] = ep.packH[1] = packRows[1];
+                    ep.pack_rph = plan[0].RPH;
+                } else if (n == N - 2) {
+                    // the last-mode stream reads the pairing factor of mode N-2
+                    if (use_her) ep.packH[0] = ep.packH[1] = packLast;
+                    else ep.packA[0] = ep.packA[1] = packLast;
+                    ep.pack_rph = plan[N - 1].RPH;
+                }
+            }
+            cudaError_t e = launch_epilogue(ep, st, pdl && !timer);
             if (e != cudaSuccess) return cuda_fail(e, "epilogue");
         }
         return NTF_OK;
@@ -376,13 +480,17 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     if ((s = S->alloc((void**)&S->Vf, sizeof(float) * r * r)) != NTF_OK) return bail(s);
     if ((s = S->alloc((void**)&S->scal, sizeof(double) * 8)) != NTF_OK) return bail(s);
     if ((s = S->alloc((void**)&S->her, sizeof(ntf_her_state))) != NTF_OK) return bail(s);
-    size_t ws = 0;
+    // one workspace region per mode: a mode's epilogue still reads its partials while the
+    // next mode's operands are being written
+    size_t ws = 0, off_mode[NTF_MAX_ORDER];
     for (int n = 0; n < N; ++n) {
         if ((s = plan_mttkrp(S->vs, r, n, &S->plan[n])) != NTF_OK) return bail(s);
         if ((s = configure_mttkrp(S->vs, S->plan[n])) != NTF_OK) return bail(s);
-        ws = std::max(ws, S->plan[n].total);
+        off_mode[n] = ws;
+        ws += (S->plan[n].total + 255) & ~size_t(255);
     }
     if ((s = S->alloc(&S->ws_mt, ws)) != NTF_OK) return bail(s);
+    for (int n = 0; n < N; ++n) S->wsm[n] = static_cast<unsigned char*>(S->ws_mt) + off_mode[n];
     if ((s = S->alloc(&S->ws_bcd, bcd_workspace(maxrows))) != NTF_OK) return bail(s);
     S->fused = S->o.method == NTF_HALS && S->o.inner_max == 1 && r <= 32;
     if (S->fused) {
@@ -390,6 +498,18 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
         if ((s = S->alloc((void**)&S->gpart, sizeof(float) * (size_t)blocks * 2 * r * r)) != NTF_OK) return bail(s);
         if ((s = S->alloc((void**)&S->ipart, sizeof(double) * (size_t)blocks)) != NTF_OK) return bail(s);
         if ((s = S->alloc((void**)&S->qpart, sizeof(double) * (size_t)blocks)) != NTF_OK) return bail(s);
+        S->direct = N == 3 && S->plan[0].tc && S->plan[1].tc && S->plan[2].tc;
+        if (S->direct) {
+            // packed operands, zero outside the factor rows and columns
+            const size_t rows_b = (size_t)S->plan[0].n_kc * 2 * S->plan[0].RPH * 128;
+            const size_t last_b = (size_t)S->plan[2].nb * tc_last_b_bytes(S->plan[2].RPH);
+            for (int k = 0; k < 2; ++k) {
+                if ((s = S->alloc((void**)&S->packRows[k], rows_b)) != NTF_OK) return bail(s);
+                NTF_CUDA_TRY(cudaMemsetAsync(S->packRows[k], 0, rows_b, st));
+            }
+            if ((s = S->alloc((void**)&S->packLast, last_b)) != NTF_OK) return bail(s);
+            NTF_CUDA_TRY(cudaMemsetAsync(S->packLast, 0, last_b, st));
+        }
     }
     S->ws_res_bytes = (((sizeof(float) * (size_t)S->vu.n_o * round_up(r, 4)) + 255) & ~size_t(255)) +
                       sizeof(double) * (size_t)std::max(stream_red_blocks(), 1);
@@ -436,6 +556,8 @@ static ntf_status capture_graph(Solver* S, int iters, cudaStream_t st) {
         cudaGraphExecDestroy(S->gexec);
         S->gexec = nullptr;
     }
+    ntf_status sp = S->ensure_prepped(st);   // before the capture: the graph holds whole iterations
+    if (sp != NTF_OK) return sp;
     S->ev_used = 0;   // the graph's event records use the first timers of the pool
     S->iter_seq = 0;  // the graph's first iteration is timed (when timing is on)
     cudaGraph_t g;
@@ -460,6 +582,10 @@ static ntf_status capture_graph(Solver* S, int iters, cudaStream_t st) {
 
 static ntf_status run_solver(Solver* S, int iters, cudaStream_t st) {
     if (iters < 0) return fail(NTF_EINVAL, "iters must be >= 0");
+    if (iters > 0) {
+        ntf_status s = S->ensure_prepped(st);
+        if (s != NTF_OK) return s;
+    }
     const bool graph = S->o.use_graph && st != nullptr;
     if (!graph) {
         for (int k = 0; k < iters; ++k) {

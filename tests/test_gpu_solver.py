@@ -236,3 +236,22 @@ def test_solver_pgd_her_300cube_r32():
     assert np.isfinite(rep.f_true_last) and rep.f_true_last < rep1.f_true_last
     assert all(bool((A >= 0).all()) for A in F)
     assert rep.f_true_last == pytest.approx(ntf.residual_sq(Td, F).item(), rel=1e-6)
+
+
+@pytest.mark.parametrize("her", [True, False])
+def test_solver_trajectory_bf16_tensor_core_path(her):
+    # the bf16 (tensor-core, 3-way) fused path against the oracle run on the same
+    # bf16-rounded tensor; the MTTKRP's hi/lo factor split rounds at ~2^-17, so F-hat
+    # agrees to 1e-5 ||T||^2
+    import paper_2001_04321_gb300 as ntf
+    dims, r, iters = (60, 50, 40), 6, 30
+    T, init, buf, d, ld, Fd = _setup(dims, r, 1e-2, 4321)
+    Tq = oracle.bf16_to_f64(oracle.round_bf16(T))
+    fh, rs, rep = _trajectory(buf, d, ld, Fd, iters, ntf.Opts(her=her, max_iters=iters, compute_dtype="bf16"))
+    _, tr = oracle.solve(Tq, init, iters, her=her)
+    same = np.cumprod(rs == tr.restart).astype(bool)
+    k = int(same.sum())
+    assert k >= 10
+    np.testing.assert_allclose(fh[:k], tr.fhat[:k], rtol=0, atol=1e-5 * oracle.norm_sq(Tq))
+    if not her:
+        assert rs.sum() == 0
