@@ -140,7 +140,7 @@ __global__ void k_prep(const PrepParams P) {
     const float* src_fc = P.Fc ? pairing_factor_c(B, P.order - 1, n, cbuf)
                                : P.FcT ? pairing_factor_c(B, P.fct_mode, n, cbuf) : nullptr;
     const float* src_fi = P.Fi ? pairing_factor_c(B, P.order - 2, n, cbuf) : nullptr;
-    const int64_t nFc = P.Fc ? P.Fc_rows_out * P.RP : P.FcT ? (int64_t)P.n_kc * 2 * P.RPH * 64 : 0;
+    const int64_t nFc = P.Fc ? P.Fc_rows_out * P.RP : P.FcT ? (int64_t)P.n_kc * 2 * P.RPH * (P.fct_tf32 ? 32 : 64) : 0;
     const int64_t nFi = P.Fi ? P.Ii * P.RP : 0;
     const int64_t nW = P.W ? P.n_o * P.RP : 0;
     const int64_t total = nFc + nFi + nW;
@@ -153,6 +153,23 @@ __global__ void k_prep(const PrepParams P) {
                 const int64_t i = k / P.RP;
                 const int p = (int)(k % P.RP);
                 P.Fc[k] = (i < P.C && p < P.r) ? src[i * P.r + p] : 0.f;
+            } else if (P.fct_tf32) {
+                // 3xTF32 B operand: F_hi | F_lo = tf32(F), tf32(F - F_hi) as FP32 words, 32-row chunks of 128-byte rows
+                const float* src = src_fc;
+                const int N = 2 * P.RPH;
+                const int kl = (int)(k % 32);
+                const int nn = (int)((k / 32) % N);
+                const int64_t kc = k / (32 * (int64_t)N);
+                const int64_t i = kc * 32 + kl;
+                const int p = nn < P.RPH ? nn : nn - P.RPH;
+                const float x = (i < P.fct_rows && p < P.r) ? src[i * P.r + p] : 0.f;
+                uint32_t h;
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+                const float hi = __uint_as_float(h);
+                uint32_t l;
+                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+                reinterpret_cast<float*>(P.FcT)[((kc * N + nn) * 128 + (((kl >> 2) ^ (nn & 7)) << 4) + (kl & 3) * 4) / 4] =
+                    nn < P.RPH ? hi : __uint_as_float(l);
             } else {
                 // tensor-core B operand: bf16 hi | lo columns, 128-byte rows, swizzled like a TMA box
                 const float* src = src_fc;
@@ -200,7 +217,7 @@ __global__ void k_prep(const PrepParams P) {
 
 cudaError_t launch_prep(const PrepParams& P, cudaStream_t st, bool pdl) {
     const int64_t total = (int64_t)32 * P.r * P.r +
-                          (P.Fc ? P.Fc_rows_out * P.RP : P.FcT ? (int64_t)P.n_kc * 2 * P.RPH * 64 : 0) +
+                          (P.Fc ? P.Fc_rows_out * P.RP : P.FcT ? (int64_t)P.n_kc * 2 * P.RPH * (P.fct_tf32 ? 32 : 64) : 0) +
                           (P.Fi ? P.Ii * P.RP : 0) + (P.W ? P.n_o * P.RP : 0);
     int64_t g = (total + 255) / 256;
     if (g > 2 * num_sms()) g = 2 * num_sms();

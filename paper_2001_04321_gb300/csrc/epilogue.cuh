@@ -32,7 +32,8 @@ struct PrepParams {
     __nv_bfloat16* FcT;                 // tensor-core operand (64-row chunks, bf16 hi|lo), or nullptr
     int fct_mode;                       // mode packed into FcT
     int64_t fct_rows;                   // its rows
-    int RPH, n_kc;                      // n_kc: 64-row chunks of FcT
+    int RPH, n_kc;                      // n_kc: chunks of FcT (64 rows; 32 rows for tf32)
+    int fct_tf32;                       // FcT in the 3xTF32 layout (FP32 words) instead of bf16
     float* Fi;                          // packed second-to-last factor (FFMA stream), or nullptr
     float* W;                           // weight table
     unsigned int* sched;                // tile counter of the next stream (set to 0 here), or nullptr

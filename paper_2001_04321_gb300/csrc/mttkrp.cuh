@@ -26,7 +26,8 @@ enum class ModeKind { Inner, Outer, Last };
 
 struct MttkrpPlan {
     ModeKind kind;
-    bool tc;             // tcgen05 kernels (bf16 storage, rank <= 32)
+    bool tc;             // tcgen05 kernels (bf16 storage, or fp32 rows modes via TF32; rank <= 32)
+    bool tf32;           // ... the 3xTF32 rows kernel for fp32 storage
     int RPH;             // tc: rank rounded up to 8 (B operand holds hi | lo, N = 2 RPH)
     int mode, rank, RP, R, n_pb;
     int I_T, O_T;

@@ -8,6 +8,7 @@
 #include "mttkrp_tc.cuh"
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -115,6 +116,14 @@ static void choose_tile(int64_t Ii, int64_t n_o, int max_IT, bool prefer_small, 
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+static bool tf32_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("NTF_TF32");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
 ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     if (rank < 1 || rank > NTF_MAX_RANK) return fail(NTF_EINVAL, "rank must be in [1, 64]");
     if (mode < 0 || mode >= v.order) return fail(NTF_EINVAL, "mode out of range");
@@ -130,9 +139,12 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
         P.R = 32;
     }
     P.n_pb = P.RP / P.R;
-    P.tc = v.dtype == NTF_BF16 && rank <= 32;
-    P.RPH = (int)round_up(rank, 8);
     P.kind = mode == v.order - 1 ? ModeKind::Last : mode == v.order - 2 ? ModeKind::Inner : ModeKind::Outer;
+    // bf16: tensor cores for every mode; fp32: the FFMA kernels, or with NTF_TF32=1 the 3xTF32
+    // rows kernel for the modes before the last
+    P.tf32 = v.dtype == NTF_F32 && rank <= 32 && P.kind != ModeKind::Last && tf32_enabled();
+    P.tc = (v.dtype == NTF_BF16 && rank <= 32) || P.tf32;
+    P.RPH = (int)round_up(rank, 8);
     // inner mode: the tensor-core kernel keeps one slot per tile, so the smallest inner
     // extent (fewest tiles per output row) is preferred; the FFMA kernel the largest
     if (P.kind == ModeKind::Inner) choose_tile(v.Ii, v.n_o, 32, P.tc, &P.I_T, &P.O_T);
@@ -141,7 +153,7 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     P.nb = ceil_div(v.Ii, P.I_T);
     P.n_ot = ceil_div(v.n_o, P.O_T);
     P.n_tiles = P.nb * P.n_ot;
-    P.n_kc = (int)ceil_div(v.C, kStageCols);
+    P.n_kc = (int)ceil_div(v.C, P.tf32 ? 32 : kStageCols);   // tf32: 32 fp32 columns per chunk
     const int sms = num_sms();
     const int cb_cols = P.tc ? 128 : kStageCols;
     P.n_cb = (int)ceil_div(v.C, cb_cols);
@@ -152,7 +164,7 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
         if (gs > P.n_tiles) gs = (int)P.n_tiles;
         P.G = gs;
     } else {
-        const int per_sm = (P.tc && 2 * tc_rows_smem(P.RPH) <= 227 * 1024) ? 2 : 1;
+        const int per_sm = (P.tc && !P.tf32 && 2 * tc_rows_smem(P.RPH) <= 227 * 1024) ? 2 : 1;
         P.G = (int)std::min<int64_t>(P.n_tiles, (int64_t)sms * per_sm);
     }
     // tensor-core row kernels take tiles at run time and keep one slot per tile; the
@@ -240,6 +252,30 @@ __global__ void k_pack_fct(const float* __restrict__ A, int64_t rows, int r, int
         const __nv_bfloat16 v = n < RPH ? hi : __float2bfloat16_rn(x - __bfloat162float(hi));
         const int64_t byte = (kc * N + n) * 128 + (((kl >> 3) ^ (n & 7)) << 4) + (kl & 7) * 2;
         out[byte / 2] = v;
+    }
+}
+
+// The 3xTF32 operand: F_hi = tf32(F) | F_lo = tf32(F - F_hi) as FP32 words, 32-row chunks of
+// 2 RPH rows x 128 B, 16-byte groups swizzled as a 128-byte-swizzled TMA box.
+__global__ void k_pack_fct_tf32(const float* __restrict__ A, int64_t rows, int r, int RPH, int n_kc,
+                                float* __restrict__ out) {
+    const int N = 2 * RPH;
+    const int64_t total = (int64_t)n_kc * N * 32;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int kl = (int)(idx % 32);
+        const int n = (int)((idx / 32) % N);
+        const int64_t kc = idx / (32 * (int64_t)N);
+        const int64_t k = kc * 32 + kl;
+        const int p = n < RPH ? n : n - RPH;
+        const float x = (k < rows && p < r) ? A[k * r + p] : 0.f;
+        uint32_t h;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+        const float hi = __uint_as_float(h);
+        uint32_t l;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+        const int64_t byte = (kc * N + n) * 128 + (((kl >> 2) ^ (n & 7)) << 4) + (kl & 3) * 4;
+        out[byte / 4] = n < RPH ? hi : __uint_as_float(l);
     }
 }
 
@@ -412,9 +448,10 @@ ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* wor
             T.job = fused->job;
         }
         grid = P.kind == ModeKind::Last ? dim3(P.G, P.n_cb, 1) : dim3(P.G, 1, 1);
-        smem = P.kind == ModeKind::Last ? tc_last_smem(P.RPH) : tc_rows_smem(P.RPH);
+        smem = P.tf32 ? tf32_rows_smem(P.RPH) : P.kind == ModeKind::Last ? tc_last_smem(P.RPH) : tc_rows_smem(P.RPH);
         if (timer && timer->start) NTF_CUDA_TRY(record_timer_event(timer->start, st));
-        e = launch_stream_tc(kind, P.RPH, grid, smem, st, *map, T, pdl && !timer);
+        e = P.tf32 ? launch_stream_tf32(kind, P.RPH, grid, smem, st, *map, T, pdl && !timer)
+                   : launch_stream_tc(kind, P.RPH, grid, smem, st, *map, T, pdl && !timer);
     } else {
         if (P.kind == ModeKind::Last) {
             grid = dim3(P.G, P.n_cb, P.n_pb);
@@ -444,7 +481,11 @@ ntf_status run_mttkrp(const TensorView& v, const MttkrpPlan& P, const float* con
 
     // 1. packed factors and weight table
     if (P.kind != ModeKind::Last) {
-        if (P.tc) {
+        if (P.tf32) {
+            k_pack_fct_tf32<<<grid_for((int64_t)P.n_kc * 2 * P.RPH * 32, 256), 256, 0, st>>>(
+                factors[N - 1], v.C, r, P.RPH, P.n_kc, Fc);
+            NTF_LAUNCH_CHECK("k_pack_fct_tf32");
+        } else if (P.tc) {
             k_pack_fct<<<grid_for((int64_t)P.n_kc * 2 * P.RPH * 64, 256), 256, 0, st>>>(
                 factors[N - 1], v.C, r, P.RPH, P.n_kc, reinterpret_cast<__nv_bfloat16*>(Fc));
             NTF_LAUNCH_CHECK("k_pack_fct");
@@ -513,6 +554,12 @@ ntf_status configure_mttkrp(const TensorView& v, const MttkrpPlan& P) {
     const int kind = P.kind == ModeKind::Inner ? 0 : P.kind == ModeKind::Outer ? 1 : 2;
     CUtensorMap dummy;
     std::memset(&dummy, 0, sizeof(dummy));
+    if (P.tf32) {
+        TcParams T{};
+        cudaError_t e = launch_stream_tf32(kind, P.RPH, dim3(0, 1, 1), tf32_rows_smem(P.RPH), nullptr, dummy, T);
+        if (e != cudaSuccess) return cuda_fail(e, "configure MTTKRP kernel");
+        return NTF_OK;
+    }
     if (P.tc) {
         TcParams T{};
         const size_t smem = P.kind == ModeKind::Last ? tc_last_smem(P.RPH) : tc_rows_smem(P.RPH);

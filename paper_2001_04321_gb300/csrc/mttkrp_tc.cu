@@ -604,6 +604,373 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
     named_bar_sync(2, 160);
 }
 
+// ----------------------------------------------------------------------------
+// TF32 rows kernel: FP32 tensor storage, modes < N-1 (step a1 for the FP32 form)
+//
+// The tensor core reads TF32 (10 explicit mantissa bits), so both operands are
+// split: T ~ T_hi + T_lo with T_hi = tf32(T) and T_lo = tf32(T - T_hi), both rounded to
+// nearest (the tensor core would otherwise truncate the remainder), F likewise.  Per 32-column chunk the accumulator
+// takes T_hi [F_hi | F_lo] and T_lo [F_hi | F_lo] (8 MMA steps, N = 2 RPH: at M = 128
+// the shape wants N a multiple of 16); the rounded remainders leave an error of about
+// 2^-22 relative per product, at FP32 level.  Four converter warps split each landed tile in shared memory (T_hi
+// in place, T_lo beside it) before the MMA warp may use it.
+//
+// Warps: 0-3 epilogue (as in k_tc_rows), 4 scheduler + TMA producer, 5 MMA issuer
+// and TMEM owner, 6-9 converters.  One CTA per SM.
+// ----------------------------------------------------------------------------
+constexpr int kTfThreads = 320;
+constexpr int kTfStages = 5;
+constexpr int kTfBars = 512;          // barrier block: 3 per stage, 8 accumulator, drain, 8 tile ring, slot, ring
+constexpr int kTfBox = 16384;          // 128 rows x 32 fp32
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Instruction descriptor, kind::tf32: FP32 accumulate, A and B TF32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+template <int RPH, bool INNER>
+__global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
+    constexpr int N = 2 * RPH;
+    constexpr int kB = N * 128;                       // factor chunk: N rows x 32 fp32 (swizzled)
+    constexpr int kStage = 2 * kTfBox + kB;           // T_hi | T_lo | B, a multiple of 1024
+    constexpr uint32_t kIdescHL = idesc_tf32(128, N);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* base_ptr = smem_raw + (base - raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base_ptr + kTfStages * kStage);
+    uint64_t* conv = full + kTfStages;          // [stage]: split by the 4 converter warps
+    uint64_t* empty = conv + kTfStages;
+    uint64_t* tfull = empty + kTfStages;        // [kDbuf]
+    uint64_t* tempty = tfull + kDbuf;           // [kDbuf]
+    uint64_t* drain = tempty + kDbuf;
+    uint64_t* sfull = drain + 1;                // [kTileRing]
+    uint64_t* sempty = sfull + kTileRing;       // [kTileRing]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + kTileRing);
+    int* tile_ring = reinterpret_cast<int*>(tmem_slot + 1);
+    float* zsum = reinterpret_cast<float*>(base_ptr + kTfStages * kStage + kTfBars);   // [2][4][32]
+    float* red = zsum + 2 * 4 * 32;                                                  // [128][RPH]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTfStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], 4);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < kDbuf; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(drain, 1);
+        for (int k = 0; k < kTileRing; ++k) {
+            mbar_init(&sfull[k], 1);
+            mbar_init(&sempty[k], 9);           // MMA thread, 4 epilogue warps, 4 converter warps
+        }
+        fence_mbar_init();
+    }
+    if (warp == 5) tmem_alloc(tmem_slot, 64 * kDbuf);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // CTA g's first tile is tile g; its first tensor chunks go out before the wait
+    const int first_tile = g_first_tile(P.n_tiles);
+    const int npre = first_tile >= 0 ? (P.n_kc < kTfStages ? P.n_kc : kTfStages) : 0;
+    if (warp == 4 && lane == 0) {
+        prefetch_tensormap(&tmap);
+        if (first_tile >= 0) {
+            int64_t ib, ot;
+            tile_coords<INNER>(P, first_tile, ib, ot);
+            for (int kc = 0; kc < npre; ++kc) {
+                mbar_arrive_expect_tx(&full[kc], (uint32_t)(kTfBox + kB));
+                tma_load_3d(base_ptr + kc * kStage, &tmap, &full[kc], kc * 32, (int)(ib * P.I_T), (int)(ot * P.O_T));
+            }
+        }
+    }
+    pdl_wait();
+    pdl_trigger();
+
+    if (warp == 4) {
+        // ------------------------- scheduler + producer -------------------------
+        if (lane == 0) {
+            const unsigned char* FcT = P.cur ? P.FcTb[__ldcg(P.cur + P.fct_sel)] : P.FcT;
+            int stage = 0;
+            uint32_t phase = 0;
+            int64_t issued = 0;
+            for (int64_t s = 0;; ++s) {
+                const int slot = (int)(s % kTileRing);
+                if (!mbar_wait_bounded(&sempty[slot], (uint32_t)((s / kTileRing) & 1) ^ 1u)) {
+                    record_device_error(P.err, kErrWaitEmpty);
+                    break;
+                }
+                int t = first_tile;
+                if (s > 0) {
+                    const unsigned int grab = atomicAdd(P.sched, 1u) + (unsigned int)gridDim.x;
+                    t = grab < (unsigned int)P.n_tiles ? (int)grab : -1;
+                }
+                tile_ring[slot] = t;
+                mbar_arrive(&sfull[slot]);
+                if (t < 0) break;
+                int64_t ib, ot;
+                tile_coords<INNER>(P, t, ib, ot);
+                bool ok = true;
+                for (int kc = 0; kc < P.n_kc; ++kc) {
+                    unsigned char* st = base_ptr + stage * kStage;
+                    if (s == 0 && kc < npre) {
+                        bulk_load(st + 2 * kTfBox, FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
+                    } else {
+                        if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
+                            record_device_error(P.err, kErrWaitEmpty);
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full[stage], (uint32_t)(kTfBox + kB));
+                        tma_load_3d(st, &tmap, &full[stage], kc * 32, (int)(ib * P.I_T), (int)(ot * P.O_T));
+                        bulk_load(st + 2 * kTfBox, FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
+                    }
+                    ++issued;
+                    if (++stage == kTfStages) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+            }
+            drain_stages(full, stage, phase, issued, P.err);
+        }
+        return;
+    }
+
+    if (warp >= 6) {
+        // ------------------------------ converters ------------------------------
+        // row m of every landed tile: T_hi written in place, T_lo beside it, at the same
+        // swizzled byte offsets (the split is elementwise)
+        const int m = (warp - 6) * 32 + lane;
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int64_t s = 0; ok; ++s) {
+            const int slot = (int)(s % kTileRing);
+            if (!warp_wait(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
+                if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                break;
+            }
+            const int t = tile_ring[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sempty[slot]);
+            if (t < 0) break;
+            for (int kc = 0; kc < P.n_kc; ++kc) {
+                if (!warp_wait(&full[stage], phase)) {
+                    if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                    ok = false;
+                    break;
+                }
+                float4* hi = reinterpret_cast<float4*>(base_ptr + stage * kStage + m * 128);
+                float4* lo = reinterpret_cast<float4*>(base_ptr + stage * kStage + kTfBox + m * 128);
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    // rows are 128 B apart: eight lanes of a quarter-warp take eight different
+                    // 16-byte groups of their rows, so every access is free of bank conflicts
+                    const int j = jj ^ (m & 7);
+                    const float4 v = hi[j];
+                    const float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+                    hi[j] = h;
+                    lo[j] = make_float4(tf32_round(v.x - h.x), tf32_round(v.y - h.y), tf32_round(v.z - h.z),
+                                        tf32_round(v.w - h.w));
+                }
+                fence_proxy_async_smem();   // the tensor core reads what these threads wrote
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&conv[stage]);
+                if (++stage == kTfStages) { stage = 0; phase ^= 1u; }
+            }
+        }
+        return;
+    }
+
+    if (warp == 5) {
+        // ------------------------------ MMA issuer ------------------------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int64_t gq = 0;
+            bool ok = true;
+            for (int64_t s = 0; ok; ++s) {
+                const int slot = (int)(s % kTileRing);
+                if (!mbar_wait_bounded(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
+                    record_device_error(P.err, kErrWaitFull);
+                    break;
+                }
+                const int t = tile_ring[slot];
+                mbar_arrive(&sempty[slot]);
+                if (t < 0) break;
+                for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
+                    const int d = (int)(gq % kDbuf);
+                    if (!mbar_wait_bounded(&tempty[d], (uint32_t)((gq / kDbuf) & 1) ^ 1u) ||
+                        !mbar_wait_bounded(&conv[stage], phase)) {
+                        record_device_error(P.err, kErrWaitFull);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t ah = base + stage * kStage;
+                    const uint32_t al = ah + kTfBox;
+                    const uint32_t b0 = ah + 2 * kTfBox;
+                    const uint32_t dt = tmem + (uint32_t)(d * 64);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)   // T_hi x [F_hi | F_lo]
+                        tc_mma_tf32(dt, smem_desc_sw128(ah + kk * 32, 16, 1024), smem_desc_sw128(b0 + kk * 32, 16, 1024),
+                                    kIdescHL, kk > 0 ? 1u : 0u);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)   // T_lo x [F_hi | F_lo] (M = 128 wants N a multiple of 16)
+                        tc_mma_tf32(dt, smem_desc_sw128(al + kk * 32, 16, 1024), smem_desc_sw128(b0 + kk * 32, 16, 1024),
+                                    kIdescHL, 1u);
+                    tc_commit(&empty[stage]);
+                    tc_commit(&tfull[d]);
+                    if (++stage == kTfStages) { stage = 0; phase ^= 1u; }
+                }
+            }
+            tc_commit(drain);
+            if (!mbar_wait_bounded(drain, 0)) record_device_error(P.err, kErrWaitDrain);
+        }
+        __syncwarp();
+        named_bar_sync(2, 160);
+        tc_fence_after();
+        tmem_dealloc(tmem, 64 * kDbuf);
+        return;
+    }
+
+    // ------------------------------ epilogue (warps 0-3) ------------------------------
+    gram_job_run(P.job, (int)blockIdx.x * 4 + warp, (int)gridDim.x * 4);
+    const float* Wt = P.cur ? P.Wb[__ldcg(P.cur + P.w_sel) ^ P.w_flip] : P.W;
+    const float* Fit = P.cur ? P.Fib[__ldcg(P.cur + P.fi_sel) ^ P.fi_flip] : P.Fi;
+    const int m = threadIdx.x;                       // tile row = TMEM lane
+    const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+    bool ok = true;
+    int64_t gq = 0;
+    int parity = 0;
+    for (int64_t s = 0; ok; ++s) {
+        const int slot = (int)(s % kTileRing);
+        if (!warp_wait(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
+            if (lane == 0) record_device_error(P.err, kErrWaitFull);
+            break;
+        }
+        const int t = tile_ring[slot];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sempty[slot]);
+        if (t < 0) break;
+        int64_t ib, ot;
+        tile_coords<INNER>(P, t, ib, ot);
+        float w[RPH];
+        bool row_live;
+        if (INNER) {
+            const int64_t o = ot * P.O_T + m / P.I_T;
+            row_live = o < P.n_o && ib * P.I_T + m % P.I_T < P.Ii;
+            const float* src = Wt + (row_live ? o : 0) * P.ldw;
+#pragma unroll
+            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(src + p) : 0.f;
+        } else {
+            const int64_t i = ib * 128 + m;
+            row_live = i < P.Ii;
+            const float* src = Fit + (row_live ? i : 0) * P.ldw;
+#pragma unroll
+            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(src + p) : 0.f;
+        }
+        float y[RPH];
+#pragma unroll
+        for (int p = 0; p < RPH; ++p) y[p] = 0.f;
+        for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
+            const int d = (int)(gq % kDbuf);
+            if (ok && !warp_wait(&tfull[d], (uint32_t)((gq / kDbuf) & 1))) {
+                if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                ok = false;
+            }
+            if (ok) {
+                tc_fence_after();
+                float yc[RPH];
+                read_rows<RPH>(tmem_row, d * 64, yc);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[d]);
+#pragma unroll
+                for (int p = 0; p < RPH; ++p) y[p] += yc[p];
+            }
+        }
+        if (INNER) {
+            float z[RPH];
+#pragma unroll
+            for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
+            for (int off = 16; off >= P.I_T; off >>= 1)
+#pragma unroll
+                for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
+            if (lane < P.I_T) {
+#pragma unroll
+                for (int p = 0; p < RPH; ++p) red[(warp * 32 + lane) * RPH + p] = z[p];
+            }
+            named_bar_sync(1, 128);
+            if (ok) {
+                for (int idx = m; idx < P.I_T * P.r; idx += 128) {
+                    const int b = idx / P.r, p = idx - b * P.r;
+                    const float sacc = (red[(0 * 32 + b) * RPH + p] + red[(1 * 32 + b) * RPH + p]) +
+                                       (red[(2 * 32 + b) * RPH + p] + red[(3 * 32 + b) * RPH + p]);
+                    P.part[((int64_t)t * P.I_T + b) * P.RP + p] = sacc;
+                }
+            }
+            named_bar_sync(1, 128);
+        } else {
+            float z[RPH];
+#pragma unroll
+            for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
+            float mine = 0.f;
+#pragma unroll
+            for (int p = 0; p < RPH; ++p)
+                if (p == lane) mine = z[p];
+            float* zs = zsum + parity * 128;
+            zs[warp * 32 + lane] = mine;
+            named_bar_sync(1, 128);
+            if (warp == 0 && lane < P.r && ok) {
+                const float s4 = (zs[lane] + zs[32 + lane]) + (zs[64 + lane] + zs[96 + lane]);
+                P.part[(int64_t)t * P.RP + lane] = s4;
+            }
+            parity ^= 1;
+        }
+    }
+    tc_fence_before();
+    named_bar_sync(2, 160);
+}
+
+template <int RPH>
+cudaError_t launch_tf32_impl(int kind, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
+                             const TcParams& P, bool pdl) {
+    typedef void (*Kern)(const CUtensorMap, const TcParams);
+    Kern k = kind == 0 ? (Kern)k_tf32_rows<RPH, true> : (Kern)k_tf32_rows<RPH, false>;
+    static size_t set_bytes[2] = {0, 0};
+    if (set_bytes[kind] < smem) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        set_bytes[kind] = smem;
+    }
+    if (grid.x == 0) return cudaSuccess;
+    return launch_kernel(k, grid, dim3(kTfThreads), smem, st, pdl, map, P);
+}
+
 template <int RPH>
 cudaError_t launch_tc_impl(int kind, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
                            const TcParams& P, bool pdl) {
@@ -632,6 +999,22 @@ size_t tc_last_smem(int rph) {
 }
 // bytes of the packed A_{N-2} operand of the last-mode kernel per 128-row block
 size_t tc_last_b_bytes(int rph) { return (size_t)2 * (2 * rph) * 128; }
+size_t tf32_rows_smem(int rph) {
+    const int N = 2 * rph;
+    return (size_t)kTfStages * (2 * kTfBox + N * 128) + 1024 + kTfBars + 2 * 4 * 32 * 4 + 128 * rph * 4;
+}
+
+cudaError_t launch_stream_tf32(int kind, int rph, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
+                               const TcParams& P, bool pdl) {
+    if (kind > 1) return cudaErrorInvalidValue;
+    switch (rph) {
+        case 8: return launch_tf32_impl<8>(kind, grid, smem, st, map, P, pdl);
+        case 16: return launch_tf32_impl<16>(kind, grid, smem, st, map, P, pdl);
+        case 24: return launch_tf32_impl<24>(kind, grid, smem, st, map, P, pdl);
+        case 32: return launch_tf32_impl<32>(kind, grid, smem, st, map, P, pdl);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_stream_tc(int kind, int rph, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
                              const TcParams& P, bool pdl) {

@@ -36,6 +36,11 @@ struct TcParams {
 size_t tc_rows_smem(int rph);
 size_t tc_last_smem(int rph);
 size_t tc_last_b_bytes(int rph);
+size_t tf32_rows_smem(int rph);
+// TF32 rows kernels for FP32 tensors (kind 0 inner, 1 outer); FcT holds F_hi | F_lo
+// as FP32 words in 32-row chunks (N rows x 128 B each, swizzled)
+cudaError_t launch_stream_tf32(int kind, int rph, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
+                               const TcParams& P, bool pdl = false);
 cudaError_t launch_stream_tc(int kind, int rph, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
                              const TcParams& P, bool pdl = false);
 

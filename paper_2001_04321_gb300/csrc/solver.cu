@@ -160,6 +160,7 @@ struct Solver {
         pp.Fc = (P.kind != ModeKind::Last && !P.tc) ? reinterpret_cast<float*>(ws + P.off_Fc) : nullptr;
         pp.FcT = P.tc ? reinterpret_cast<__nv_bfloat16*>(ws + P.off_Fc) : nullptr;
         pp.RPH = P.RPH;
+        pp.fct_tf32 = P.tf32 ? 1 : 0;
         if (P.kind == ModeKind::Last) {      // tensor-core last mode: A_{N-2}, two chunks per 128-row block
             pp.fct_mode = N - 2;
             pp.fct_rows = vs.Ii;

@@ -37,6 +37,24 @@ def _trajectory(buf, d, ld, Fd, iters, opts):
     return np.array(fh), np.array(rs), rep
 
 
+def _check_trajectory(fh, rs, tr, tnorm_sq, min_k, atol_rel=1e-6, f_true=None, f_true_ref=None):
+    """F-hat agrees with the oracle's while every restart decision has matched.  A first
+    differing decision is allowed only where the oracle's own margin F_k - F_{k-1} is
+    below what the two F-hat sequences can resolve (2 atol): a tie that rounding decides.
+    The final objective is compared only when no decision differed."""
+    atol = atol_rel * tnorm_sq
+    same = np.cumprod(rs == tr.restart).astype(bool)
+    k = int(same.sum())
+    assert k >= min_k
+    np.testing.assert_allclose(fh[:k], tr.fhat[:k], rtol=0, atol=atol)
+    if k < len(rs):
+        prev = tr.fhat[k - 1] if k > 0 else tr.fhat0[0]
+        assert abs(tr.fhat[k] - prev) <= 2 * atol, "a restart decision differs away from a tie"
+    elif f_true is not None:
+        assert abs(f_true - f_true_ref) <= 1e-3 * f_true_ref
+    return k
+
+
 @pytest.mark.parametrize("her", [True, False])
 def test_solver_trajectory_20cube(her):
     import paper_2001_04321_gb300 as ntf
@@ -47,11 +65,7 @@ def test_solver_trajectory_20cube(her):
     # identical decisions up to the first divergence; F-hat agrees there.  FP32
     # factors carry rounding of ~6e-8 relative per update, so F-hat (a difference
     # of terms of size ||T||^2) agrees to an absolute 1e-6 ||T||^2, not relatively.
-    same = np.cumprod(rs == tr.restart).astype(bool)
-    k = int(same.sum())
-    assert k >= 10
-    np.testing.assert_allclose(fh[:k], tr.fhat[:k], rtol=0, atol=1e-6 * oracle.norm_sq(T))
-    assert abs(rep.f_true_last - tr.ftrue[-1]) <= 1e-3 * tr.ftrue[-1]
+    _check_trajectory(fh, rs, tr, oracle.norm_sq(T), 10, f_true=rep.f_true_last, f_true_ref=tr.ftrue[-1])
     if not her:
         assert rs.sum() == 0
         # Alg. 1 never increases F (up to FP32 rounding of the objective)
@@ -62,24 +76,25 @@ def test_solver_4way_and_pgd():
     import paper_2001_04321_gb300 as ntf
     dims, r, iters = (10, 9, 8, 7), 4, 30
     T, init, buf, d, ld, Fd = _setup(dims, r, 1e-2, 77, recipe="sparse30")
-    F = [A.clone() for A in Fd]
-    rep = ntf.solve(buf, F, ntf.Opts(max_iters=iters), dims=d, ld=ld)
+    tn = oracle.norm_sq(T)
+    fh, rs, rep = _trajectory(buf, d, ld, [A.clone() for A in Fd], iters, ntf.Opts(max_iters=iters))
     _, tr = oracle.solve(T, init, iters, her=True, track_true=True)
-    assert abs(rep.f_true_last - tr.ftrue[-1]) <= 1e-3 * tr.ftrue[-1]
-    F = [A.clone() for A in Fd]
-    rep = ntf.solve(buf, F, ntf.Opts(max_iters=10, method="pgd", inner_max=5, her=True), dims=d, ld=ld)
+    _check_trajectory(fh, rs, tr, tn, 5, f_true=rep.f_true_last, f_true_ref=tr.ftrue[-1])
+    opts = ntf.Opts(max_iters=10, method="pgd", inner_max=5, her=True)
+    fh, rs, rep = _trajectory(buf, d, ld, [A.clone() for A in Fd], 10, opts)
     _, tr = oracle.solve(T, init, 10, her=True, method="pgd", inner_max=5, track_true=True)
-    assert abs(rep.f_true_last - tr.ftrue[-1]) <= 1e-3 * tr.ftrue[-1]
+    _check_trajectory(fh, rs, tr, tn, 5, f_true=rep.f_true_last, f_true_ref=tr.ftrue[-1])
 
 
 def test_solver_ahals_inner_loop():
     import paper_2001_04321_gb300 as ntf
     dims, r, iters = (30, 25, 20), 4, 20
     T, init, buf, d, ld, Fd = _setup(dims, r, 1e-2, 91)
-    F = [A.clone() for A in Fd]
-    rep = ntf.solve(buf, F, ntf.Opts(max_iters=iters, inner_max=50, inner_tol=1e-2), dims=d, ld=ld)
+    opts = ntf.Opts(max_iters=iters, inner_max=50, inner_tol=1e-2)
+    fh, rs, rep = _trajectory(buf, d, ld, [A.clone() for A in Fd], iters, opts)
     _, tr = oracle.solve(T, init, iters, her=True, inner_max=50, inner_tol=1e-2, track_true=True)
-    assert abs(rep.f_true_last - tr.ftrue[-1]) <= 1e-3 * tr.ftrue[-1]
+    # this trajectory has a near-tie at iteration 14 (F_14 - F_13 = -8e-8 ||T||^2)
+    _check_trajectory(fh, rs, tr, oracle.norm_sq(T), 10, f_true=rep.f_true_last, f_true_ref=tr.ftrue[-1])
 
 
 def test_solver_outputs_feasible_and_match_report():
