@@ -116,12 +116,14 @@ static void choose_tile(int64_t Ii, int64_t n_o, int max_IT, bool prefer_small, 
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-static bool tf32_enabled() {
-    static const bool on = [] {
+// NTF_TF32: unset or 1 = 3xTF32 tensor-core kernels for every mode of an FP32 tensor,
+// 2 = for the modes before the last only, 0 = the FFMA kernels
+static int tf32_mode() {
+    static const int m = [] {
         const char* e = std::getenv("NTF_TF32");
-        return e && e[0] == '1';
+        return (e && (e[0] == '0' || e[0] == '2')) ? e[0] - '0' : 1;
     }();
-    return on;
+    return m;
 }
 
 ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
@@ -140,14 +142,15 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     }
     P.n_pb = P.RP / P.R;
     P.kind = mode == v.order - 1 ? ModeKind::Last : mode == v.order - 2 ? ModeKind::Inner : ModeKind::Outer;
-    // bf16: tensor cores for every mode; fp32: the FFMA kernels, or with NTF_TF32=1 the 3xTF32
-    // rows kernel for the modes before the last
-    P.tf32 = v.dtype == NTF_F32 && rank <= 32 && P.kind != ModeKind::Last && tf32_enabled();
+    // bf16: tensor cores for every mode; fp32: the FFMA kernels, or the 3xTF32 tensor-core
+    // kernels as NTF_TF32 selects
+    P.tf32 = v.dtype == NTF_F32 && rank <= 32 && (tf32_mode() == 1 || (tf32_mode() == 2 && P.kind != ModeKind::Last));
     P.tc = (v.dtype == NTF_BF16 && rank <= 32) || P.tf32;
     P.RPH = (int)round_up(rank, 8);
     // inner mode: the tensor-core kernel keeps one slot per tile, so the smallest inner
     // extent (fewest tiles per output row) is preferred; the FFMA kernel the largest
     if (P.kind == ModeKind::Inner) choose_tile(v.Ii, v.n_o, 32, P.tc, &P.I_T, &P.O_T);
+    else if (P.kind == ModeKind::Last && P.tf32) { P.I_T = 32; P.O_T = 1; }     // tf32 last mode: 32-row tiles
     else if (P.kind == ModeKind::Outer || P.tc) { P.I_T = 128; P.O_T = 1; }   // tc last mode: W(o,:) per tile
     else choose_tile(v.Ii, v.n_o, 128, false, &P.I_T, &P.O_T);
     P.nb = ceil_div(v.Ii, P.I_T);
@@ -182,8 +185,8 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     }
     size_t off = 0;
     P.off_Fc = off;
-    if (P.tc && P.kind == ModeKind::Last)
-        off = align256(off + (size_t)P.nb * tc_last_b_bytes(P.RPH));     // packed A_{N-2} blocks
+    if (P.tc && P.kind == ModeKind::Last)                               // packed A_{N-2} blocks
+        off = align256(off + (size_t)P.nb * (P.tf32 ? (size_t)(2 * P.RPH) * 128 : tc_last_b_bytes(P.RPH)));
     else if (P.tc)
         off = align256(off + (size_t)P.n_kc * (2 * P.RPH) * 128);       // packed A_{N-1} chunks
     else
@@ -495,7 +498,12 @@ ntf_status run_mttkrp(const TensorView& v, const MttkrpPlan& P, const float* con
             NTF_LAUNCH_CHECK("k_pack(A_last)");
         }
     }
-    if (P.tc && P.kind == ModeKind::Last) {
+    if (P.tf32 && P.kind == ModeKind::Last) {
+        // TF32 operand of the last mode: A_{N-2} in 32-row chunks, one per tile row block
+        k_pack_fct_tf32<<<grid_for((int64_t)P.nb * 2 * P.RPH * 32, 256), 256, 0, st>>>(factors[N - 2], v.Ii, r,
+                                                                                          P.RPH, (int)P.nb, Fc);
+        NTF_LAUNCH_CHECK("k_pack_fct_tf32(A_second_to_last)");
+    } else if (P.tc && P.kind == ModeKind::Last) {
         // tensor-core operand of the last mode: A_{N-2} in 64-row chunks, two per 128-row block
         const int chunks = (int)(2 * P.nb);
         k_pack_fct<<<grid_for((int64_t)chunks * 2 * P.RPH * 64, 256), 256, 0, st>>>(

@@ -53,26 +53,31 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn_major, 
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                       uint32_t accumulate) {
+// D (+)= A x B, both operands in shared memory, issued by one elected lane of a converged
+// warp: the whole warp runs the issue loop, so descriptors and addresses stay warp-uniform
+// (measured 2.6x faster per MMA than a loop run by one lane alone).
+__device__ __forceinline__ void tc_mma_elect(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+// commit by the elected lane (the one that issued the MMAs it tracks)
+__device__ __forceinline__ void tc_commit_elect(uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
@@ -262,45 +267,44 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
 
     if (warp == 5) {
         // ------------------------------ MMA issuer ------------------------------
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            int64_t gq = 0;   // accumulator (chunk) counter of this CTA
-            bool ok = true;
-            for (int64_t s = 0; ok; ++s) {
-                const int slot = (int)(s % kTileRing);
-                if (!mbar_wait_bounded(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
-                    record_device_error(P.err, kErrWaitFull);
+        // the whole warp runs the loop; one elected lane issues the MMAs and commits
+        int stage = 0;
+        uint32_t phase = 0;
+        int64_t gq = 0;   // accumulator (chunk) counter of this CTA
+        bool ok = true;
+        for (int64_t s = 0; ok; ++s) {
+            const int slot = (int)(s % kTileRing);
+            if (!warp_wait(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
+                if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                break;
+            }
+            const int t = tile_ring[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sempty[slot]);
+            if (t < 0) break;
+            for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
+                const int d = (int)(gq % kDbuf);
+                if (!warp_wait(&tempty[d], (uint32_t)((gq / kDbuf) & 1) ^ 1u) || !warp_wait(&full[stage], phase)) {
+                    if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                    ok = false;
                     break;
                 }
-                const int t = tile_ring[slot];
-                mbar_arrive(&sempty[slot]);
-                if (t < 0) break;
-                for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
-                    const int d = (int)(gq % kDbuf);
-                    if (!mbar_wait_bounded(&tempty[d], (uint32_t)((gq / kDbuf) & 1) ^ 1u) ||
-                        !mbar_wait_bounded(&full[stage], phase)) {
-                        record_device_error(P.err, kErrWaitFull);
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t a0 = base + stage * kStage;
-                    const uint32_t b0 = a0 + kBoxBytes;
-                    const uint32_t dt = tmem + (uint32_t)(d * 64);
+                tc_fence_after();
+                const uint32_t a0 = base + stage * kStage;
+                const uint32_t b0 = a0 + kBoxBytes;
+                const uint32_t dt = tmem + (uint32_t)(d * 64);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        tc_mma(dt, smem_desc_sw128(a0 + kk * 32, 16, 1024), smem_desc_sw128(b0 + kk * 32, 16, 1024),
-                               kIdesc, kk > 0 ? 1u : 0u);
-                    tc_commit(&empty[stage]);          // frees the stage once these MMAs have read it
-                    tc_commit(&tfull[d]);              // this chunk's accumulator is complete
-                    if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
-                }
+                for (int kk = 0; kk < 4; ++kk)
+                    tc_mma_elect(dt, smem_desc_sw128(a0 + kk * 32, 16, 1024), smem_desc_sw128(b0 + kk * 32, 16, 1024),
+                                 kIdesc, kk > 0 ? 1u : 0u);
+                tc_commit_elect(&empty[stage]);          // frees the stage once these MMAs have read it
+                tc_commit_elect(&tfull[d]);              // this chunk's accumulator is complete
+                if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
             }
-            // make sure nothing is still running on the tensor cores before TMEM is freed
-            tc_commit(drain);
-            if (!mbar_wait_bounded(drain, 0)) record_device_error(P.err, kErrWaitDrain);
         }
+        // make sure nothing is still running on the tensor cores before TMEM is freed
+        tc_commit_elect(drain);
+        if (!warp_wait(drain, 0) && lane == 0) record_device_error(P.err, kErrWaitDrain);
         __syncwarp();
         named_bar_sync(2, 160);
         tc_fence_after();
@@ -521,36 +525,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
     }
 
     if (warp == 5) {
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            int64_t tl = 0;
-            for (int64_t t = t_beg; t < t_end; ++t, ++tl) {
-                const int d = (int)(tl % kLastDbuf);
-                if (!mbar_wait_bounded(&tempty[d], (uint32_t)((tl / kLastDbuf) & 1) ^ 1u) ||
-                    !mbar_wait_bounded(&full[stage], phase)) {
-                    record_device_error(P.err, kErrWaitFull);
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t a0 = base + stage * kStage;
-                const uint32_t b0 = a0 + kT;
-                const uint32_t dt = tmem + (uint32_t)(d * 64);
-#pragma unroll
-                for (int kk = 0; kk < 8; ++kk) {
-                    // A: 16 tile rows (two 8-row groups 1024 B apart), 128 columns in two
-                    // 64-column blocks 16 KB apart; B: K-atom kk/4, 32-byte step kk%4
-                    const uint64_t ad = smem_desc_sw128(a0 + kk * 2048, kBoxBytes, 1024);
-                    const uint64_t bd = smem_desc_sw128(b0 + (kk >> 2) * (N * 128) + (kk & 3) * 32, 16, 1024);
-                    tc_mma(dt, ad, bd, kIdesc, kk > 0 ? 1u : 0u);
-                }
-                tc_commit(&empty[stage]);
-                tc_commit(&tfull[d]);
-                if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
+        // the whole warp runs the loop; one elected lane issues the MMAs and commits
+        int stage = 0;
+        uint32_t phase = 0;
+        int64_t tl = 0;
+        for (int64_t t = t_beg; t < t_end; ++t, ++tl) {
+            const int d = (int)(tl % kLastDbuf);
+            if (!warp_wait(&tempty[d], (uint32_t)((tl / kLastDbuf) & 1) ^ 1u) || !warp_wait(&full[stage], phase)) {
+                if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                break;
             }
-            tc_commit(drain);
-            if (!mbar_wait_bounded(drain, 0)) record_device_error(P.err, kErrWaitDrain);
+            tc_fence_after();
+            const uint32_t a0 = base + stage * kStage;
+            const uint32_t b0 = a0 + kT;
+            const uint32_t dt = tmem + (uint32_t)(d * 64);
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                // A: 16 tile rows (two 8-row groups 1024 B apart), 128 columns in two
+                // 64-column blocks 16 KB apart; B: K-atom kk/4, 32-byte step kk%4
+                const uint64_t ad = smem_desc_sw128(a0 + kk * 2048, kBoxBytes, 1024);
+                const uint64_t bd = smem_desc_sw128(b0 + (kk >> 2) * (N * 128) + (kk & 3) * 32, 16, 1024);
+                tc_mma_elect(dt, ad, bd, kIdesc, kk > 0 ? 1u : 0u);
+            }
+            tc_commit_elect(&empty[stage]);
+            tc_commit_elect(&tfull[d]);
+            if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
         }
+        tc_commit_elect(drain);
+        if (!warp_wait(drain, 0) && lane == 0) record_device_error(P.err, kErrWaitDrain);
         __syncwarp();
         named_bar_sync(2, 160);
         tc_fence_after();
@@ -609,19 +611,41 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
 //
 // The tensor core reads TF32 (10 explicit mantissa bits), so both operands are
 // split: T ~ T_hi + T_lo with T_hi = tf32(T) and T_lo = tf32(T - T_hi), both rounded to
-// nearest (the tensor core would otherwise truncate the remainder), F likewise.  Per 32-column chunk the accumulator
-// takes T_hi [F_hi | F_lo] and T_lo [F_hi | F_lo] (8 MMA steps, N = 2 RPH: at M = 128
-// the shape wants N a multiple of 16); the rounded remainders leave an error of about
-// 2^-22 relative per product, at FP32 level.  Four converter warps split each landed tile in shared memory (T_hi
-// in place, T_lo beside it) before the MMA warp may use it.
+// nearest (the tensor core would otherwise truncate the remainder), F likewise.  Per
+// 32-column chunk the MMAs take T_hi [F_hi | F_lo] and T_lo [F_hi | F_lo] (8 steps,
+// N = 2 RPH: at M = 128 the shape wants N a multiple of 16) into three accumulators (see
+// kTfAccCols); the rounded remainders leave an error of about 2^-22 relative per product.
 //
-// Warps: 0-3 epilogue (as in k_tc_rows), 4 scheduler + TMA producer, 5 MMA issuer
-// and TMEM owner, 6-9 converters.  One CTA per SM.
+// The split tensor never goes back to shared memory.  Four converter warps read each
+// landed box (one row per thread), release the box at once, and write T_hi | T_lo into
+// one of two tensor-memory A slots; the MMAs take A from tensor memory and B (the packed
+// factor chunk) from a ring of its own.  Shared memory carries each tensor byte twice
+// (the TMA write and the converter's read), and eight boxes are in flight.
+//
+// Warps: 0-3 epilogue (as in k_tc_rows), 4 scheduler + TMA producer, 5 MMA issuer and
+// TMEM owner, 6-13 converters (two groups of four), 14 second MMA issuer, 15 factor-chunk
+// producer.  One CTA per SM; 512 TMEM columns (two chunks of three 64-column accumulators,
+// then the two A slots).
 // ----------------------------------------------------------------------------
-constexpr int kTfThreads = 320;
-constexpr int kTfStages = 5;
-constexpr int kTfBars = 512;          // barrier block: 3 per stage, 8 accumulator, drain, 8 tile ring, slot, ring
+constexpr int kTfThreads = 512;
+constexpr int kTfConvGroups = 2;       // converter groups of 4 warps (6-9, 10-13), taking chunks in turn
+constexpr int kTfMmaWarp2 = 14;        // second MMA warp (the first is warp 5); the two take chunks in turn
+constexpr int kTfBWarp = 15;           // factor-chunk producer
+constexpr int kTfRaw = 8;              // tensor boxes in flight
+constexpr int kTfB = 8;                // factor chunks in flight (a producer warp of their own, so
+                                       // that the boxes run ahead of the MMAs by the whole box ring)
+constexpr int kTfA = 2;                // tensor-memory A slots of 64 columns (T_hi | T_lo)
+// Accumulators: the tensor core's FP32 accumulation drops about half a unit in the last place
+// (toward zero) whenever it adds into a large running sum, measured as a bias of -3e-8 per
+// such add.  One accumulator per chunk took 7 of them (-2.3e-7 in every result), so each
+// chunk now has three: T_hi's K steps 0-1, T_hi's steps 2-3 and all of T_lo (whose sum stays
+// small), summed in FP32 by the epilogue: 2 large adds.
+constexpr int kTfDbuf = 2;             // chunks whose accumulators are in flight
+constexpr int kTfAccCols = 192;        // three 64-column accumulators per chunk
 constexpr int kTfBox = 16384;          // 128 rows x 32 fp32
+constexpr int kTfBars = 512;           // barrier block (50 barriers, TMEM slot, tile ring)
+constexpr uint32_t kTfAcol = kTfAccCols * kTfDbuf;
+constexpr uint32_t kTfCols = 512;
 
 __device__ __forceinline__ float tf32_round(float x) {
     uint32_t r;
@@ -634,87 +658,172 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t accumulate) {
+// D (+)= A x B with A (M x 8, one TF32 per 32-bit column, row m in lane m) in tensor memory,
+// issued by one elected lane of a converged warp.  The whole warp runs the issue
+// loop, so its descriptors and addresses stay warp-uniform; a loop run by one lane alone
+// was measured at about 1.6x the time per MMA.
+__device__ __forceinline__ void tc_mma_tf32_ts_elect(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                                     uint32_t idesc, uint32_t accumulate) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+
+
+// 32 lanes x 32 bit, 32 consecutive columns per thread
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// a chunk's three accumulators (64 columns apart), summed in a fixed order
+template <int RPH>
+__device__ __forceinline__ void read_acc3(uint32_t tmem_row, int col0, float (&y)[RPH]) {
+    float y0[RPH], y1[RPH];
+    read_rows<RPH>(tmem_row, col0, y0);
+    read_rows<RPH>(tmem_row, col0 + 64, y1);
+    read_rows<RPH>(tmem_row, col0 + 128, y);
+#pragma unroll
+    for (int p = 0; p < RPH; ++p) y[p] = (y0[p] + y1[p]) + y[p];
+}
+
+// wait until the last min(issued, R) loads of a ring of R stages have landed
+__device__ __forceinline__ void drain_ring(uint64_t* full, int R, int64_t issued, int* err) {
+    const int64_t lo = issued > R ? issued - R : 0;
+    for (int64_t i = issued - 1; i >= lo; --i)
+        if (!mbar_wait_bounded(&full[i % R], (uint32_t)((i / R) & 1))) {
+            record_device_error(err, kErrWaitDrain);
+            break;
+        }
 }
 
 template <int RPH, bool INNER>
 __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
     constexpr int N = 2 * RPH;
     constexpr int kB = N * 128;                       // factor chunk: N rows x 32 fp32 (swizzled)
-    constexpr int kStage = 2 * kTfBox + kB;           // T_hi | T_lo | B, a multiple of 1024
-    constexpr uint32_t kIdescHL = idesc_tf32(128, N);
+    constexpr uint32_t kIdesc = idesc_tf32(128, N);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char* base_ptr = smem_raw + (base - raw);
-    uint64_t* full = reinterpret_cast<uint64_t*>(base_ptr + kTfStages * kStage);
-    uint64_t* conv = full + kTfStages;          // [stage]: split by the 4 converter warps
-    uint64_t* empty = conv + kTfStages;
-    uint64_t* tfull = empty + kTfStages;        // [kDbuf]
-    uint64_t* tempty = tfull + kDbuf;           // [kDbuf]
-    uint64_t* drain = tempty + kDbuf;
-    uint64_t* sfull = drain + 1;                // [kTileRing]
-    uint64_t* sempty = sfull + kTileRing;       // [kTileRing]
+    unsigned char* boxes = base_ptr;                               // [kTfRaw][kTfBox]
+    unsigned char* bring = base_ptr + kTfRaw * kTfBox;             // [kTfB][kB]
+    unsigned char* misc = bring + kTfB * kB;
+    uint64_t* rfull = reinterpret_cast<uint64_t*>(misc);           // box landed
+    uint64_t* rempty = rfull + kTfRaw;                             // box read by the 4 converter warps
+    uint64_t* bfull = rempty + kTfRaw;                             // factor chunk landed
+    uint64_t* bempty = bfull + kTfB;                               // factor chunk used by the MMAs
+    uint64_t* afull = bempty + kTfB;                               // A slot written by the 4 converter warps
+    uint64_t* aempty = afull + kTfA;                               // A slot used by the MMAs
+    uint64_t* tfull = aempty + kTfA;                               // [kTfDbuf] accumulators ready
+    uint64_t* tempty = tfull + kTfDbuf;                            // [kTfDbuf] accumulators read
+    uint64_t* drain = tempty + kTfDbuf;                            // [2]: one per MMA warp
+    uint64_t* sfull = drain + 2;                                   // [kTileRing]
+    uint64_t* sempty = sfull + kTileRing;                          // [kTileRing]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + kTileRing);
     int* tile_ring = reinterpret_cast<int*>(tmem_slot + 1);
-    float* zsum = reinterpret_cast<float*>(base_ptr + kTfStages * kStage + kTfBars);   // [2][4][32]
-    float* red = zsum + 2 * 4 * 32;                                                  // [128][RPH]
+    float* zsum = reinterpret_cast<float*>(misc + kTfBars);        // [2][4][32]
+    float* red = zsum + 2 * 4 * 32;                                // [128][RPH]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kTfStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&conv[s], 4);
-            mbar_init(&empty[s], 1);
+        for (int s = 0; s < kTfRaw; ++s) {
+            mbar_init(&rfull[s], 1);
+            mbar_init(&rempty[s], 4);
         }
-        for (int b = 0; b < kDbuf; ++b) {
+        for (int s = 0; s < kTfB; ++s) {
+            mbar_init(&bfull[s], 1);
+            mbar_init(&bempty[s], 1);
+        }
+        for (int s = 0; s < kTfA; ++s) {
+            mbar_init(&afull[s], 4);
+            mbar_init(&aempty[s], 1);
+        }
+        for (int b = 0; b < kTfDbuf; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 4);
         }
-        mbar_init(drain, 1);
+        mbar_init(&drain[0], 1);
+        mbar_init(&drain[1], 1);
         for (int k = 0; k < kTileRing; ++k) {
             mbar_init(&sfull[k], 1);
-            mbar_init(&sempty[k], 9);           // MMA thread, 4 epilogue warps, 4 converter warps
+            mbar_init(&sempty[k], 7 + 4 * kTfConvGroups);   // 2 MMA, 4 epilogue, B producer, converters
         }
         fence_mbar_init();
     }
-    if (warp == 5) tmem_alloc(tmem_slot, 64 * kDbuf);
+    if (warp == 5) tmem_alloc(tmem_slot, kTfCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    // CTA g's first tile is tile g; its first tensor chunks go out before the wait
+    // CTA g's first tile is tile g; its first tensor boxes go out before the wait
     const int first_tile = g_first_tile(P.n_tiles);
-    const int npre = first_tile >= 0 ? (P.n_kc < kTfStages ? P.n_kc : kTfStages) : 0;
+    const int npre = first_tile >= 0 ? (P.n_kc < kTfRaw ? P.n_kc : kTfRaw) : 0;
     if (warp == 4 && lane == 0) {
         prefetch_tensormap(&tmap);
         if (first_tile >= 0) {
             int64_t ib, ot;
             tile_coords<INNER>(P, first_tile, ib, ot);
             for (int kc = 0; kc < npre; ++kc) {
-                mbar_arrive_expect_tx(&full[kc], (uint32_t)(kTfBox + kB));
-                tma_load_3d(base_ptr + kc * kStage, &tmap, &full[kc], kc * 32, (int)(ib * P.I_T), (int)(ot * P.O_T));
+                mbar_arrive_expect_tx(&rfull[kc], (uint32_t)kTfBox);
+                tma_load_3d(boxes + kc * kTfBox, &tmap, &rfull[kc], kc * 32, (int)(ib * P.I_T), (int)(ot * P.O_T));
             }
         }
     }
     pdl_wait();
     pdl_trigger();
 
-    if (warp == 4) {
-        // ------------------------- scheduler + producer -------------------------
+    if (warp == kTfBWarp) {
+        // --------------------- factor-chunk producer (all tiles alike) ---------------------
         if (lane == 0) {
             const unsigned char* FcT = P.cur ? P.FcTb[__ldcg(P.cur + P.fct_sel)] : P.FcT;
-            int stage = 0;
-            uint32_t phase = 0;
-            int64_t issued = 0;
-            for (int64_t s = 0;; ++s) {
+            int64_t g = 0, b_issued = 0;
+            bool ok = true;
+            for (int64_t s = 0; ok; ++s) {
+                const int slot = (int)(s % kTileRing);
+                if (!mbar_wait_bounded(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
+                    record_device_error(P.err, kErrWaitFull);
+                    break;
+                }
+                const int t = tile_ring[slot];
+                mbar_arrive(&sempty[slot]);
+                if (t < 0) break;
+                for (int kc = 0; kc < P.n_kc; ++kc, ++g) {
+                    const int bs = (int)(g % kTfB);
+                    if (!mbar_wait_bounded(&bempty[bs], (uint32_t)((g / kTfB) & 1) ^ 1u)) {
+                        record_device_error(P.err, kErrWaitEmpty);
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&bfull[bs], (uint32_t)kB);
+                    bulk_load(bring + bs * kB, FcT + (int64_t)kc * kB, (uint32_t)kB, &bfull[bs]);
+                    b_issued = g + 1;
+                }
+            }
+            drain_ring(bfull, kTfB, b_issued, P.err);
+        }
+        return;
+    }
+
+    if (warp == 4) {
+        // ------------------------- scheduler + box producer -------------------------
+        if (lane == 0) {
+            int64_t g = 0;                      // chunks of this CTA
+            int64_t raw_issued = npre;
+            bool ok = true;
+            for (int64_t s = 0; ok; ++s) {
                 const int slot = (int)(s % kTileRing);
                 if (!mbar_wait_bounded(&sempty[slot], (uint32_t)((s / kTileRing) & 1) ^ 1u)) {
                     record_device_error(P.err, kErrWaitEmpty);
@@ -730,38 +839,36 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
                 if (t < 0) break;
                 int64_t ib, ot;
                 tile_coords<INNER>(P, t, ib, ot);
-                bool ok = true;
-                for (int kc = 0; kc < P.n_kc; ++kc) {
-                    unsigned char* st = base_ptr + stage * kStage;
-                    if (s == 0 && kc < npre) {
-                        bulk_load(st + 2 * kTfBox, FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
-                    } else {
-                        if (!mbar_wait_bounded(&empty[stage], phase ^ 1u)) {
+                for (int kc = 0; kc < P.n_kc; ++kc, ++g) {
+                    if (!(s == 0 && kc < npre)) {
+                        const int rs = (int)(g % kTfRaw);
+                        if (!mbar_wait_bounded(&rempty[rs], (uint32_t)((g / kTfRaw) & 1) ^ 1u)) {
                             record_device_error(P.err, kErrWaitEmpty);
                             ok = false;
                             break;
                         }
-                        mbar_arrive_expect_tx(&full[stage], (uint32_t)(kTfBox + kB));
-                        tma_load_3d(st, &tmap, &full[stage], kc * 32, (int)(ib * P.I_T), (int)(ot * P.O_T));
-                        bulk_load(st + 2 * kTfBox, FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
+                        mbar_arrive_expect_tx(&rfull[rs], (uint32_t)kTfBox);
+                        tma_load_3d(boxes + rs * kTfBox, &tmap, &rfull[rs], kc * 32, (int)(ib * P.I_T),
+                                    (int)(ot * P.O_T));
+                        raw_issued = g + 1;
                     }
-                    ++issued;
-                    if (++stage == kTfStages) { stage = 0; phase ^= 1u; }
                 }
-                if (!ok) break;
             }
-            drain_stages(full, stage, phase, issued, P.err);
+            drain_ring(rfull, kTfRaw, raw_issued, P.err);
         }
         return;
     }
 
-    if (warp >= 6) {
+    if (warp >= 6 && warp < kTfMmaWarp2) {
         // ------------------------------ converters ------------------------------
-        // row m of every landed tile: T_hi written in place, T_lo beside it, at the same
-        // swizzled byte offsets (the split is elementwise)
-        const int m = (warp - 6) * 32 + lane;
-        int stage = 0;
-        uint32_t phase = 0;
+        // warp w may reach TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31: tile row m = TMEM lane m.
+        // Group cg converts the chunks g with g % kTfConvGroups == cg, so that the latency of
+        // one chunk's loads, conversion and tensor-memory stores overlaps the next chunk's.
+        const int cg = (warp - 6) >> 2;
+        const int q = warp & 3;
+        const int m = q * 32 + lane;
+        const uint32_t tmem_lane = tmem + ((uint32_t)(q * 32) << 16);
+        int64_t g = 0;
         bool ok = true;
         for (int64_t s = 0; ok; ++s) {
             const int slot = (int)(s % kTileRing);
@@ -773,83 +880,107 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
             __syncwarp();
             if (lane == 0) mbar_arrive(&sempty[slot]);
             if (t < 0) break;
-            for (int kc = 0; kc < P.n_kc; ++kc) {
-                if (!warp_wait(&full[stage], phase)) {
+            for (int kc = 0; kc < P.n_kc; ++kc, ++g) {
+                if ((int)(g % kTfConvGroups) != cg) continue;
+                const int rs = (int)(g % kTfRaw);
+                if (!warp_wait(&rfull[rs], (uint32_t)((g / kTfRaw) & 1))) {
                     if (lane == 0) record_device_error(P.err, kErrWaitFull);
                     ok = false;
                     break;
                 }
-                float4* hi = reinterpret_cast<float4*>(base_ptr + stage * kStage + m * 128);
-                float4* lo = reinterpret_cast<float4*>(base_ptr + stage * kStage + kTfBox + m * 128);
+                // logical 16-byte group j of row m sits at group j ^ (m & 7) (128-byte swizzle);
+                // the eight lanes of a quarter-warp thus touch eight different bank groups
+                const float4* row = reinterpret_cast<const float4*>(boxes + rs * kTfBox + m * 128);
+                float v[32];
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    // rows are 128 B apart: eight lanes of a quarter-warp take eight different
-                    // 16-byte groups of their rows, so every access is free of bank conflicts
-                    const int j = jj ^ (m & 7);
-                    const float4 v = hi[j];
-                    const float4 h = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
-                    hi[j] = h;
-                    lo[j] = make_float4(tf32_round(v.x - h.x), tf32_round(v.y - h.y), tf32_round(v.z - h.z),
-                                        tf32_round(v.w - h.w));
+                for (int j = 0; j < 8; ++j) {
+                    const float4 x = row[j ^ (m & 7)];
+                    v[4 * j] = x.x;
+                    v[4 * j + 1] = x.y;
+                    v[4 * j + 2] = x.z;
+                    v[4 * j + 3] = x.w;
                 }
-                fence_proxy_async_smem();   // the tensor core reads what these threads wrote
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&conv[stage]);
-                if (++stage == kTfStages) { stage = 0; phase ^= 1u; }
+                if (lane == 0) mbar_arrive(&rempty[rs]);
+                uint32_t hi[32], lo[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const float h = tf32_round(v[i]);
+                    hi[i] = __float_as_uint(h);
+                    lo[i] = __float_as_uint(tf32_round(v[i] - h));
+                }
+                const int a = (int)(g % kTfA);
+                if (!warp_wait(&aempty[a], (uint32_t)((g / kTfA) & 1) ^ 1u)) {
+                    if (lane == 0) record_device_error(P.err, kErrWaitEmpty);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                tmem_st32(tmem_lane + kTfAcol + (uint32_t)(a * 64), hi);
+                tmem_st32(tmem_lane + kTfAcol + (uint32_t)(a * 64 + 32), lo);
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&afull[a]);
             }
         }
         return;
     }
 
-    if (warp == 5) {
-        // ------------------------------ MMA issuer ------------------------------
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            int64_t gq = 0;
-            bool ok = true;
-            for (int64_t s = 0; ok; ++s) {
-                const int slot = (int)(s % kTileRing);
-                if (!mbar_wait_bounded(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
-                    record_device_error(P.err, kErrWaitFull);
+    if (warp == 5 || warp == kTfMmaWarp2) {
+        // ------------------------------ MMA issuers ------------------------------
+        // Each warp runs the loop as a whole, and one elected lane issues the MMAs and
+        // commits.  A single issuing warp was measured at about 105 cycles per MMA whatever
+        // the shape, so two warps take the chunks in turn (mg = chunk parity): the
+        // accumulators, A slot and factor slot of a chunk all have the chunk's parity.
+        const int mg = warp == 5 ? 0 : 1;
+        int64_t g = 0;
+        bool ok = true;
+        for (int64_t s = 0; ok; ++s) {
+            const int slot = (int)(s % kTileRing);
+            if (!warp_wait(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
+                if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                break;
+            }
+            const int t = tile_ring[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sempty[slot]);
+            if (t < 0) break;
+            for (int kc = 0; kc < P.n_kc; ++kc, ++g) {
+                if ((int)(g & 1) != mg) continue;
+                const int d = (int)(g % kTfDbuf), a = (int)(g % kTfA), bs = (int)(g % kTfB);
+                if (!warp_wait(&tempty[d], (uint32_t)((g / kTfDbuf) & 1) ^ 1u) ||
+                    !warp_wait(&afull[a], (uint32_t)((g / kTfA) & 1)) ||
+                    !warp_wait(&bfull[bs], (uint32_t)((g / kTfB) & 1))) {
+                    if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                    ok = false;
                     break;
                 }
-                const int t = tile_ring[slot];
-                mbar_arrive(&sempty[slot]);
-                if (t < 0) break;
-                for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
-                    const int d = (int)(gq % kDbuf);
-                    if (!mbar_wait_bounded(&tempty[d], (uint32_t)((gq / kDbuf) & 1) ^ 1u) ||
-                        !mbar_wait_bounded(&conv[stage], phase)) {
-                        record_device_error(P.err, kErrWaitFull);
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t ah = base + stage * kStage;
-                    const uint32_t al = ah + kTfBox;
-                    const uint32_t b0 = ah + 2 * kTfBox;
-                    const uint32_t dt = tmem + (uint32_t)(d * 64);
+                tc_fence_after();
+                const uint32_t b0 = base + (uint32_t)(kTfRaw * kTfBox + bs * kB);
+                const uint32_t dt = tmem + (uint32_t)(d * kTfAccCols);
+                const uint32_t at = tmem + kTfAcol + (uint32_t)(a * 64);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)   // T_hi x [F_hi | F_lo]
-                        tc_mma_tf32(dt, smem_desc_sw128(ah + kk * 32, 16, 1024), smem_desc_sw128(b0 + kk * 32, 16, 1024),
-                                    kIdescHL, kk > 0 ? 1u : 0u);
+                for (int kk = 0; kk < 4; ++kk)     // T_lo x [F_hi | F_lo] into the third accumulator
+                    tc_mma_tf32_ts_elect(dt + 128, at + 32 + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
+                                         kk > 0 ? 1u : 0u);
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)   // T_lo x [F_hi | F_lo] (M = 128 wants N a multiple of 16)
-                        tc_mma_tf32(dt, smem_desc_sw128(al + kk * 32, 16, 1024), smem_desc_sw128(b0 + kk * 32, 16, 1024),
-                                    kIdescHL, 1u);
-                    tc_commit(&empty[stage]);
-                    tc_commit(&tfull[d]);
-                    if (++stage == kTfStages) { stage = 0; phase ^= 1u; }
-                }
+                for (int kk = 0; kk < 4; ++kk)     // T_hi x [F_hi | F_lo]: steps 0-1, then 2-3
+                    tc_mma_tf32_ts_elect(dt + (kk >> 1) * 64, at + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024),
+                                         kIdesc, (kk & 1) ? 1u : 0u);
+                tc_commit_elect(&aempty[a]);
+                tc_commit_elect(&bempty[bs]);
+                tc_commit_elect(&tfull[d]);
             }
-            tc_commit(drain);
-            if (!mbar_wait_bounded(drain, 0)) record_device_error(P.err, kErrWaitDrain);
         }
+        tc_commit_elect(&drain[mg]);
+        if (!warp_wait(&drain[mg], 0) && lane == 0) record_device_error(P.err, kErrWaitDrain);
         __syncwarp();
-        named_bar_sync(2, 160);
-        tc_fence_after();
-        tmem_dealloc(tmem, 64 * kDbuf);
+        named_bar_sync(2, 192);
+        if (warp == 5) {
+            tc_fence_after();
+            tmem_dealloc(tmem, kTfCols);
+        }
         return;
     }
 
@@ -893,15 +1024,15 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
 #pragma unroll
         for (int p = 0; p < RPH; ++p) y[p] = 0.f;
         for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
-            const int d = (int)(gq % kDbuf);
-            if (ok && !warp_wait(&tfull[d], (uint32_t)((gq / kDbuf) & 1))) {
+            const int d = (int)(gq % kTfDbuf);
+            if (ok && !warp_wait(&tfull[d], (uint32_t)((gq / kTfDbuf) & 1))) {
                 if (lane == 0) record_device_error(P.err, kErrWaitFull);
                 ok = false;
             }
             if (ok) {
                 tc_fence_after();
                 float yc[RPH];
-                read_rows<RPH>(tmem_row, d * 64, yc);
+                read_acc3<RPH>(tmem_row, d * kTfAccCols, yc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[d]);
@@ -953,15 +1084,269 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
         }
     }
     tc_fence_before();
-    named_bar_sync(2, 160);
+    named_bar_sync(2, 192);
+}
+
+// ----------------------------------------------------------------------------
+// TF32 last-mode kernel: FP32 tensor storage, mode N-1 (step a1 for the FP32 form)
+//
+// M_{N-1}(c, :) = sum_o W(o, :) (*) sum_i T(o, i, c) A_{N-2}(i, :).  A tile is one outer
+// index o, 32 rows i and a block of 128 columns c (four 32 x 32 boxes, 16 KB).  The MMAs
+// take A = the split tile transposed (lane = column c, K = row i) from tensor memory and
+// B = the packed A_{N-2} rows of the tile (32-row chunks, as the rows kernel's factor
+// operand), and the epilogue folds W(o, :) x accumulator into registers, one column per
+// thread, over the CTA's contiguous tile range.  The converter warp of lane quarter q reads
+// box q one row (32 columns) per instruction, free of bank conflicts, and writes its column's
+// 32 split values into its tensor-memory lane.  Warps, rings, MMA issue and the split are
+// those of k_tf32_rows; tiles are static ranges (grid = CTAs x column blocks).
+// ----------------------------------------------------------------------------
+template <int RPH>
+__global__ void __launch_bounds__(kTfThreads, 1) k_tf32_last(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
+    constexpr int N = 2 * RPH;
+    constexpr int kB = N * 128;                       // A_{N-2} chunk: N rows x 32 fp32 (swizzled)
+    constexpr int kSub = 4096;                        // one 32 x 32 box
+    constexpr uint32_t kIdesc = idesc_tf32(128, N);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* base_ptr = smem_raw + (base - raw);
+    unsigned char* boxes = base_ptr;                               // [kTfRaw][4 x kSub]
+    unsigned char* bring = base_ptr + kTfRaw * kTfBox;             // [kTfB][kB]
+    unsigned char* misc = bring + kTfB * kB;
+    uint64_t* rfull = reinterpret_cast<uint64_t*>(misc);
+    uint64_t* rempty = rfull + kTfRaw;
+    uint64_t* bfull = rempty + kTfRaw;
+    uint64_t* bempty = bfull + kTfB;
+    uint64_t* afull = bempty + kTfB;
+    uint64_t* aempty = afull + kTfA;
+    uint64_t* tfull = aempty + kTfA;
+    uint64_t* tempty = tfull + kTfDbuf;
+    uint64_t* drain = tempty + kTfDbuf;                            // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = blockIdx.x, G = gridDim.x;
+    const int cb = blockIdx.y;
+    int64_t t_beg, t_end;
+    tile_range(P.n_tiles, g, G, t_beg, t_end);
+    const int64_t nt = t_end - t_beg;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTfRaw; ++s) {
+            mbar_init(&rfull[s], 1);
+            mbar_init(&rempty[s], 4);
+        }
+        for (int s = 0; s < kTfB; ++s) {
+            mbar_init(&bfull[s], 1);
+            mbar_init(&bempty[s], 1);
+        }
+        for (int s = 0; s < kTfA; ++s) {
+            mbar_init(&afull[s], 4);
+            mbar_init(&aempty[s], 1);
+        }
+        for (int b = 0; b < kTfDbuf; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(&drain[0], 1);
+        mbar_init(&drain[1], 1);
+        fence_mbar_init();
+    }
+    if (warp == 5) tmem_alloc(tmem_slot, kTfCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // the first tiles' boxes go out before the wait (the tensor is never written)
+    const int npre = (int)(nt < kTfRaw ? nt : kTfRaw);
+    if (warp == 4 && lane == 0) {
+        prefetch_tensormap(&tmap);
+        for (int q = 0; q < npre; ++q) {
+            const int64_t t = t_beg + q;
+            const int64_t ib = t / P.n_ot, o = t % P.n_ot;     // I_T = 32, O_T = 1
+            mbar_arrive_expect_tx(&rfull[q], (uint32_t)kTfBox);
+            for (int j = 0; j < 4; ++j)
+                tma_load_3d(boxes + q * kTfBox + j * kSub, &tmap, &rfull[q], cb * 128 + 32 * j, (int)(ib * 32), (int)o);
+        }
+    }
+    pdl_wait();
+    pdl_trigger();
+
+    if (warp == kTfBWarp) {
+        // --------------------------- A_{N-2} chunk producer ---------------------------
+        if (lane == 0) {
+            const unsigned char* FcT = P.cur ? P.FcTb[__ldcg(P.cur + P.fct_sel)] : P.FcT;
+            int64_t b_issued = 0;
+            for (int64_t q = 0; q < nt; ++q) {
+                const int64_t ib = (t_beg + q) / P.n_ot;
+                const int bs = (int)(q % kTfB);
+                if (!mbar_wait_bounded(&bempty[bs], (uint32_t)((q / kTfB) & 1) ^ 1u)) {
+                    record_device_error(P.err, kErrWaitEmpty);
+                    break;
+                }
+                mbar_arrive_expect_tx(&bfull[bs], (uint32_t)kB);
+                bulk_load(bring + bs * kB, FcT + ib * kB, (uint32_t)kB, &bfull[bs]);
+                b_issued = q + 1;
+            }
+            drain_ring(bfull, kTfB, b_issued, P.err);
+        }
+        return;
+    }
+
+    if (warp == 4) {
+        // ------------------------------- box producer -------------------------------
+        if (lane == 0) {
+            int64_t raw_issued = npre;
+            for (int64_t q = 0; q < nt; ++q) {
+                const int64_t t = t_beg + q;
+                const int64_t ib = t / P.n_ot, o = t % P.n_ot;
+                if (q >= npre) {
+                    const int rs = (int)(q % kTfRaw);
+                    if (!mbar_wait_bounded(&rempty[rs], (uint32_t)((q / kTfRaw) & 1) ^ 1u)) {
+                        record_device_error(P.err, kErrWaitEmpty);
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&rfull[rs], (uint32_t)kTfBox);
+                    for (int j = 0; j < 4; ++j)
+                        tma_load_3d(boxes + rs * kTfBox + j * kSub, &tmap, &rfull[rs], cb * 128 + 32 * j, (int)(ib * 32),
+                                    (int)o);
+                    raw_issued = q + 1;
+                }
+            }
+            drain_ring(rfull, kTfRaw, raw_issued, P.err);
+        }
+        return;
+    }
+
+    if (warp >= 6 && warp < kTfMmaWarp2) {
+        // ------------------------------ converters ------------------------------
+        // lane quarter q = column group q of the block: thread = column 32 q + lane = TMEM lane
+        const int cg = (warp - 6) >> 2;
+        const int q = warp & 3;
+        const uint32_t tmem_lane = tmem + ((uint32_t)(q * 32) << 16);
+        for (int64_t k = cg; k < nt; k += kTfConvGroups) {
+            const int rs = (int)(k % kTfRaw);
+            if (!warp_wait(&rfull[rs], (uint32_t)((k / kTfRaw) & 1))) {
+                if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                break;
+            }
+            // row i of box q: 128 bytes, 16-byte group j at j ^ (i & 7); this lane's column is
+            // in group lane / 4
+            const unsigned char* box = boxes + rs * kTfBox + q * kSub + (lane & 3) * 4;
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                v[i] = *reinterpret_cast<const float*>(box + i * 128 + (((lane >> 2) ^ (i & 7)) << 4));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&rempty[rs]);
+            uint32_t hi[32], lo[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+                const float h = tf32_round(v[i]);
+                hi[i] = __float_as_uint(h);
+                lo[i] = __float_as_uint(tf32_round(v[i] - h));
+            }
+            const int a = (int)(k % kTfA);
+            if (!warp_wait(&aempty[a], (uint32_t)((k / kTfA) & 1) ^ 1u)) {
+                if (lane == 0) record_device_error(P.err, kErrWaitEmpty);
+                break;
+            }
+            tc_fence_after();
+            tmem_st32(tmem_lane + kTfAcol + (uint32_t)(a * 64), hi);
+            tmem_st32(tmem_lane + kTfAcol + (uint32_t)(a * 64 + 32), lo);
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&afull[a]);
+        }
+        return;
+    }
+
+    if (warp == 5 || warp == kTfMmaWarp2) {
+        // ------------------------------ MMA issuers (tiles in turn) ------------------------------
+        const int mg = warp == 5 ? 0 : 1;
+        for (int64_t k = mg; k < nt; k += 2) {
+            const int d = (int)(k % kTfDbuf), a = (int)(k % kTfA), bs = (int)(k % kTfB);
+            if (!warp_wait(&tempty[d], (uint32_t)((k / kTfDbuf) & 1) ^ 1u) ||
+                !warp_wait(&afull[a], (uint32_t)((k / kTfA) & 1)) || !warp_wait(&bfull[bs], (uint32_t)((k / kTfB) & 1))) {
+                if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t b0 = base + (uint32_t)(kTfRaw * kTfBox + bs * kB);
+            const uint32_t dt = tmem + (uint32_t)(d * kTfAccCols);
+            const uint32_t at = tmem + kTfAcol + (uint32_t)(a * 64);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)     // T_lo^T x [F_hi | F_lo] into the third accumulator
+                tc_mma_tf32_ts_elect(dt + 128, at + 32 + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
+                                     kk > 0 ? 1u : 0u);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)     // T_hi^T x [F_hi | F_lo]: steps 0-1, then 2-3
+                tc_mma_tf32_ts_elect(dt + (kk >> 1) * 64, at + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
+                                     (kk & 1) ? 1u : 0u);
+            tc_commit_elect(&aempty[a]);
+            tc_commit_elect(&bempty[bs]);
+            tc_commit_elect(&tfull[d]);
+        }
+        tc_commit_elect(&drain[mg]);
+        if (!warp_wait(&drain[mg], 0) && lane == 0) record_device_error(P.err, kErrWaitDrain);
+        __syncwarp();
+        named_bar_sync(2, 192);
+        if (warp == 5) {
+            tc_fence_after();
+            tmem_dealloc(tmem, kTfCols);
+        }
+        return;
+    }
+
+    // ---------------- warps 0-3: fold W(o,:) x tile accumulator into registers ----------------
+    gram_job_run(P.job, ((int)blockIdx.y * (int)gridDim.x + (int)blockIdx.x) * 4 + warp,
+                 (int)(gridDim.x * gridDim.y) * 4);
+    const float* Wt = P.cur ? P.Wb[__ldcg(P.cur + P.w_sel) ^ P.w_flip] : P.W;
+    const int m = threadIdx.x;
+    const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+    bool ok = true;
+    float acc[RPH];
+#pragma unroll
+    for (int p = 0; p < RPH; ++p) acc[p] = 0.f;
+    for (int64_t k = 0; k < nt && ok; ++k) {
+        const int64_t o = (t_beg + k) % P.n_ot;
+        float w[RPH];
+        const float* wr = Wt + o * P.ldw;
+#pragma unroll
+        for (int p = 0; p < RPH; ++p) w[p] = p < P.r ? __ldg(wr + p) : 0.f;
+        const int d = (int)(k % kTfDbuf);
+        if (!warp_wait(&tfull[d], (uint32_t)((k / kTfDbuf) & 1))) {
+            if (lane == 0) record_device_error(P.err, kErrWaitFull);
+            ok = false;
+            break;
+        }
+        tc_fence_after();
+        float y[RPH];
+        read_acc3<RPH>(tmem_row, d * kTfAccCols, y);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[d]);
+#pragma unroll
+        for (int p = 0; p < RPH; ++p) acc[p] = fmaf(w[p], y[p], acc[p]);
+    }
+    // row m of the result = column cb*128 + m of M_{N-1}
+    const int64_t c = (int64_t)cb * 128 + m;
+    if (ok && c < P.C) {
+        float* dst = P.part + ((int64_t)g * P.Cpad + c) * P.RP;
+#pragma unroll
+        for (int p = 0; p < RPH; ++p)
+            if (p < P.r) dst[p] = acc[p];
+    }
+    tc_fence_before();
+    named_bar_sync(2, 192);
 }
 
 template <int RPH>
 cudaError_t launch_tf32_impl(int kind, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
                              const TcParams& P, bool pdl) {
     typedef void (*Kern)(const CUtensorMap, const TcParams);
-    Kern k = kind == 0 ? (Kern)k_tf32_rows<RPH, true> : (Kern)k_tf32_rows<RPH, false>;
-    static size_t set_bytes[2] = {0, 0};
+    Kern k = kind == 0 ? (Kern)k_tf32_rows<RPH, true> : kind == 1 ? (Kern)k_tf32_rows<RPH, false> : (Kern)k_tf32_last<RPH>;
+    static size_t set_bytes[3] = {0, 0, 0};
     if (set_bytes[kind] < smem) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1001,12 +1386,12 @@ size_t tc_last_smem(int rph) {
 size_t tc_last_b_bytes(int rph) { return (size_t)2 * (2 * rph) * 128; }
 size_t tf32_rows_smem(int rph) {
     const int N = 2 * rph;
-    return (size_t)kTfStages * (2 * kTfBox + N * 128) + 1024 + kTfBars + 2 * 4 * 32 * 4 + 128 * rph * 4;
+    return (size_t)kTfRaw * kTfBox + (size_t)kTfB * N * 128 + 1024 + kTfBars + 2 * 4 * 32 * 4 + 128 * rph * 4;
 }
 
 cudaError_t launch_stream_tf32(int kind, int rph, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
                                const TcParams& P, bool pdl) {
-    if (kind > 1) return cudaErrorInvalidValue;
+    if (kind > 2) return cudaErrorInvalidValue;
     switch (rph) {
         case 8: return launch_tf32_impl<8>(kind, grid, smem, st, map, P, pdl);
         case 16: return launch_tf32_impl<16>(kind, grid, smem, st, map, P, pdl);

@@ -161,10 +161,10 @@ struct Solver {
         pp.FcT = P.tc ? reinterpret_cast<__nv_bfloat16*>(ws + P.off_Fc) : nullptr;
         pp.RPH = P.RPH;
         pp.fct_tf32 = P.tf32 ? 1 : 0;
-        if (P.kind == ModeKind::Last) {      // tensor-core last mode: A_{N-2}, two chunks per 128-row block
+        if (P.kind == ModeKind::Last) {      // tensor-core last mode: A_{N-2} by row blocks
             pp.fct_mode = N - 2;
             pp.fct_rows = vs.Ii;
-            pp.n_kc = (int)(2 * P.nb);
+            pp.n_kc = (int)(P.tf32 ? P.nb : 2 * P.nb);   // 32-row chunks (tf32) or two 64-row ones
         } else {
             pp.fct_mode = N - 1;
             pp.fct_rows = vs.C;
@@ -499,7 +499,8 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
         if ((s = S->alloc((void**)&S->gpart, sizeof(float) * (size_t)blocks * 2 * r * r)) != NTF_OK) return bail(s);
         if ((s = S->alloc((void**)&S->ipart, sizeof(double) * (size_t)blocks)) != NTF_OK) return bail(s);
         if ((s = S->alloc((void**)&S->qpart, sizeof(double) * (size_t)blocks)) != NTF_OK) return bail(s);
-        S->direct = N == 3 && S->plan[0].tc && S->plan[1].tc && S->plan[2].tc;
+        // (the epilogues write the packed bf16 operand layout, so not with the TF32 kernels)
+        S->direct = N == 3 && S->plan[0].tc && S->plan[1].tc && S->plan[2].tc && !S->plan[0].tf32;
         if (S->direct) {
             // packed operands, zero outside the factor rows and columns
             const size_t rows_b = (size_t)S->plan[0].n_kc * 2 * S->plan[0].RPH * 128;

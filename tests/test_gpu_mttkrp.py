@@ -94,3 +94,51 @@ def test_mttkrp_rejects_bad_arguments():
         ntf.mttkrp(T, F, 0, workspace=ws)
     assert "workspace" in str(e.value)
     ntf.device_status()
+
+
+def test_fp32_tensor_core_mttkrp_is_unbiased():
+    # The 3xTF32 kernels sum each chunk in three tensor-core accumulators so that few adds
+    # go into a large running sum (each such add drops about half a unit toward zero).  The
+    # mean relative deviation from the oracle stays below 1.5e-7 (one accumulator per chunk
+    # gave -2.3e-7 in every mode; the FFMA kernels give about 1e-9).
+    import torch
+    import paper_2001_04321_gb300 as ntf
+    dims, r = (64, 128, 64), 16
+    T, F = _problem(dims, r, 2)
+    buf, d, ld = device_tensor(T, "f32")
+    Fd = [torch.from_numpy(A).cuda() for A in F]
+    for n in range(3):
+        M = ntf.mttkrp(buf, Fd, n, dims=d, ld=ld).cpu().numpy().astype(np.float64)
+        R = oracle.mttkrp(T, F, n)
+        assert abs(np.sum(M - R) / np.sum(R)) <= 1.5e-7, n
+
+
+_CHILD = r"""
+import sys, numpy as np, torch
+sys.path[:0] = [{root!r}, {tests!r}]
+import oracle, synth
+import paper_2001_04321_gb300 as ntf
+from gpu_helpers import device_tensor, rel_fro
+for dims, r in [((37, 23, 19), 5), ((130, 300, 70), 20), ((3, 4, 5, 6), 7)]:
+    T, _ = synth.make_tensor(dims, r, 1e-2, seed=r)
+    F = synth.make_init(dims, r, seed=r)
+    buf, d, ld = device_tensor(T, "f32")
+    Fd = [torch.from_numpy(A).cuda() for A in F]
+    for n in range(len(dims)):
+        M = ntf.mttkrp(buf, Fd, n, dims=d, ld=ld).cpu().numpy()
+        e = rel_fro(M, oracle.mttkrp(T, F, n))
+        assert e <= 1e-5, (dims, r, n, e)
+print("ok")
+"""
+
+
+@pytest.mark.parametrize("mode", ["0", "2"])
+def test_fp32_kernel_selection(mode):
+    # NTF_TF32=0 (FFMA kernels for every mode) and 2 (tensor cores before the last mode)
+    # are read once per process, so each runs in a child process
+    import os, subprocess, sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    code = _CHILD.format(root=os.path.dirname(here), tests=here)
+    env = dict(os.environ, NTF_TF32=mode)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0 and "ok" in out.stdout, out.stderr[-2000:]
