@@ -36,7 +36,8 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 TIMING_EVERY = 10
 KERNEL_SOURCES = ["paper_2001_04321_gb300/csrc/mttkrp_kernels.cuh", "paper_2001_04321_gb300/csrc/mttkrp_host.cu",
-                  "paper_2001_04321_gb300/csrc/mttkrp_tc.cuh", "paper_2001_04321_gb300/csrc/mttkrp_tc.cu"]
+                  "paper_2001_04321_gb300/csrc/mttkrp_tc.cuh", "paper_2001_04321_gb300/csrc/mttkrp_tc.cu",
+                  "paper_2001_04321_gb300/csrc/ntf_common.cuh", "paper_2001_04321_gb300/csrc/fused.cuh"]
 
 
 def kernel_hash() -> str:
