@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
 // split: T ~ T_hi + T_lo with T_hi = tf32(T) and T_lo = tf32(T - T_hi), both rounded to
 // nearest (the tensor core would otherwise truncate the remainder), F likewise.  Per
 // 32-column chunk the MMAs take T_hi [F_hi | F_lo] and T_lo [F_hi | F_lo] (8 steps,
-// N = 2 RPH: at M = 128 the shape wants N a multiple of 16) into three accumulators (see
+// N = 2 RPH: at M = 128 the shape wants N a multiple of 16) into two accumulators (see
 // kTfAccCols); the rounded remainders leave an error of about 2^-22 relative per product.
 //
 // The split tensor never goes back to shared memory.  Four converter warps read each
@@ -638,10 +638,10 @@ constexpr int kTfA = 2;                // tensor-memory A slots of 64 columns (T
 // Accumulators: the tensor core's FP32 accumulation drops about half a unit in the last place
 // (toward zero) whenever it adds into a large running sum, measured as a bias of -3e-8 per
 // such add.  One accumulator per chunk took 7 of them (-2.3e-7 in every result), so each
-// chunk now has three: T_hi's K steps 0-1, T_hi's steps 2-3 and all of T_lo (whose sum stays
-// small), summed in FP32 by the epilogue: 2 large adds.
-constexpr int kTfDbuf = 2;             // chunks whose accumulators are in flight
-constexpr int kTfAccCols = 192;        // three 64-column accumulators per chunk
+// chunk has two, summed in FP32 by the epilogue: T_lo's four K steps (whose sum stays small)
+// then T_hi's steps 0-1 in the first, T_hi's steps 2-3 in the second: 3 large adds.
+constexpr int kTfDbuf = 3;             // chunks whose accumulators are in flight
+constexpr int kTfAccCols = 128;        // two 64-column accumulators per chunk
 constexpr int kTfBox = 16384;          // 128 rows x 32 fp32
 constexpr int kTfBars = 512;           // barrier block (50 barriers, TMEM slot, tile ring)
 constexpr uint32_t kTfAcol = kTfAccCols * kTfDbuf;
@@ -688,15 +688,14 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// a chunk's three accumulators (64 columns apart), summed in a fixed order
+// a chunk's two accumulators (64 columns apart), summed in FP32
 template <int RPH>
-__device__ __forceinline__ void read_acc3(uint32_t tmem_row, int col0, float (&y)[RPH]) {
-    float y0[RPH], y1[RPH];
+__device__ __forceinline__ void read_acc2(uint32_t tmem_row, int col0, float (&y)[RPH]) {
+    float y0[RPH];
     read_rows<RPH>(tmem_row, col0, y0);
-    read_rows<RPH>(tmem_row, col0 + 64, y1);
-    read_rows<RPH>(tmem_row, col0 + 128, y);
+    read_rows<RPH>(tmem_row, col0 + 64, y);
 #pragma unroll
-    for (int p = 0; p < RPH; ++p) y[p] = (y0[p] + y1[p]) + y[p];
+    for (int p = 0; p < RPH; ++p) y[p] = y0[p] + y[p];
 }
 
 // wait until the last min(issued, R) loads of a ring of R stages have landed
@@ -961,13 +960,13 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
                 const uint32_t dt = tmem + (uint32_t)(d * kTfAccCols);
                 const uint32_t at = tmem + kTfAcol + (uint32_t)(a * 64);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)     // T_lo x [F_hi | F_lo] into the third accumulator
-                    tc_mma_tf32_ts_elect(dt + 128, at + 32 + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
+                for (int kk = 0; kk < 4; ++kk)     // T_lo x [F_hi | F_lo], first accumulator
+                    tc_mma_tf32_ts_elect(dt, at + 32 + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
                                          kk > 0 ? 1u : 0u);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)     // T_hi x [F_hi | F_lo]: steps 0-1, then 2-3
+                for (int kk = 0; kk < 4; ++kk)     // T_hi x [F_hi | F_lo]: steps 0-1 on top, 2-3 in the second
                     tc_mma_tf32_ts_elect(dt + (kk >> 1) * 64, at + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024),
-                                         kIdesc, (kk & 1) ? 1u : 0u);
+                                         kIdesc, kk == 2 ? 0u : 1u);
                 tc_commit_elect(&aempty[a]);
                 tc_commit_elect(&bempty[bs]);
                 tc_commit_elect(&tfull[d]);
@@ -1032,7 +1031,7 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
             if (ok) {
                 tc_fence_after();
                 float yc[RPH];
-                read_acc3<RPH>(tmem_row, d * kTfAccCols, yc);
+                read_acc2<RPH>(tmem_row, d * kTfAccCols, yc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[d]);
@@ -1276,13 +1275,13 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_last(const __grid_consta
             const uint32_t dt = tmem + (uint32_t)(d * kTfAccCols);
             const uint32_t at = tmem + kTfAcol + (uint32_t)(a * 64);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)     // T_lo^T x [F_hi | F_lo] into the third accumulator
-                tc_mma_tf32_ts_elect(dt + 128, at + 32 + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
+            for (int kk = 0; kk < 4; ++kk)     // T_lo^T x [F_hi | F_lo], first accumulator
+                tc_mma_tf32_ts_elect(dt, at + 32 + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
                                      kk > 0 ? 1u : 0u);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)     // T_hi^T x [F_hi | F_lo]: steps 0-1, then 2-3
+            for (int kk = 0; kk < 4; ++kk)     // T_hi^T x [F_hi | F_lo]: steps 0-1 on top, 2-3 in the second
                 tc_mma_tf32_ts_elect(dt + (kk >> 1) * 64, at + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
-                                     (kk & 1) ? 1u : 0u);
+                                     kk == 2 ? 0u : 1u);
             tc_commit_elect(&aempty[a]);
             tc_commit_elect(&bempty[bs]);
             tc_commit_elect(&tfull[d]);
@@ -1322,7 +1321,7 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_last(const __grid_consta
         }
         tc_fence_after();
         float y[RPH];
-        read_acc3<RPH>(tmem_row, d * kTfAccCols, y);
+        read_acc2<RPH>(tmem_row, d * kTfAccCols, y);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[d]);
