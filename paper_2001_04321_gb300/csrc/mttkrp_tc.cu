@@ -613,19 +613,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
 // split: T ~ T_hi + T_lo with T_hi = tf32(T) and T_lo = tf32(T - T_hi), both rounded to
 // nearest (the tensor core would otherwise truncate the remainder), F likewise.  Per
 // 32-column chunk the MMAs take T_hi [F_hi | F_lo] and T_lo [F_hi | F_lo] (8 steps,
-// N = 2 RPH: at M = 128 the shape wants N a multiple of 16) into two accumulators (see
+// N = 2 RPH: at M = 128 the shape wants N a multiple of 16) into one accumulator (see
 // kTfAccCols); the rounded remainders leave an error of about 2^-22 relative per product.
 //
 // The split tensor never goes back to shared memory.  Four converter warps read each
 // landed box (one row per thread), release the box at once, and write T_hi | T_lo into
-// one of two tensor-memory A slots; the MMAs take A from tensor memory and B (the packed
+// one of four tensor-memory A slots; the MMAs take A from tensor memory and B (the packed
 // factor chunk) from a ring of its own.  Shared memory carries each tensor byte twice
 // (the TMA write and the converter's read), and eight boxes are in flight.
 //
 // Warps: 0-3 epilogue (as in k_tc_rows), 4 scheduler + TMA producer, 5 MMA issuer and
 // TMEM owner, 6-13 converters (two groups of four), 14 second MMA issuer, 15 factor-chunk
-// producer.  One CTA per SM; 512 TMEM columns (two chunks of three 64-column accumulators,
-// then the two A slots).
+// producer.  One CTA per SM; 512 TMEM columns (four 64-column accumulators, then four A
+// slots).
 // ----------------------------------------------------------------------------
 constexpr int kTfThreads = 512;
 constexpr int kTfConvGroups = 2;       // converter groups of 4 warps (6-9, 10-13), taking chunks in turn
@@ -634,14 +634,13 @@ constexpr int kTfBWarp = 15;           // factor-chunk producer
 constexpr int kTfRaw = 8;              // tensor boxes in flight
 constexpr int kTfB = 8;                // factor chunks in flight (a producer warp of their own, so
                                        // that the boxes run ahead of the MMAs by the whole box ring)
-constexpr int kTfA = 2;                // tensor-memory A slots of 64 columns (T_hi | T_lo)
+constexpr int kTfA = 4;                // tensor-memory A slots of 64 columns (T_hi | T_lo)
 // Accumulators: the tensor core's FP32 accumulation drops about half a unit in the last place
 // (toward zero) whenever it adds into a large running sum, measured as a bias of -3e-8 per
-// such add.  One accumulator per chunk took 7 of them (-2.3e-7 in every result), so each
-// chunk has two, summed in FP32 by the epilogue: T_lo's four K steps (whose sum stays small)
-// then T_hi's steps 0-1 in the first, T_hi's steps 2-3 in the second: 3 large adds.
-constexpr int kTfDbuf = 3;             // chunks whose accumulators are in flight
-constexpr int kTfAccCols = 128;        // two 64-column accumulators per chunk
+// such add.  Taking T_hi's steps first and T_lo's after gave -2.3e-7 in every result; T_lo's
+// four K steps first (their sum stays small), then T_hi's on top, gives -6e-8.
+constexpr int kTfDbuf = 4;             // chunks whose accumulators are in flight
+constexpr int kTfAccCols = 64;         // one 64-column accumulator per chunk
 constexpr int kTfBox = 16384;          // 128 rows x 32 fp32
 constexpr int kTfBars = 512;           // barrier block (50 barriers, TMEM slot, tile ring)
 constexpr uint32_t kTfAcol = kTfAccCols * kTfDbuf;
@@ -688,15 +687,6 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// a chunk's two accumulators (64 columns apart), summed in FP32
-template <int RPH>
-__device__ __forceinline__ void read_acc2(uint32_t tmem_row, int col0, float (&y)[RPH]) {
-    float y0[RPH];
-    read_rows<RPH>(tmem_row, col0, y0);
-    read_rows<RPH>(tmem_row, col0 + 64, y);
-#pragma unroll
-    for (int p = 0; p < RPH; ++p) y[p] = y0[p] + y[p];
-}
 
 // wait until the last min(issued, R) loads of a ring of R stages have landed
 __device__ __forceinline__ void drain_ring(uint64_t* full, int R, int64_t issued, int* err) {
@@ -964,9 +954,8 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
                     tc_mma_tf32_ts_elect(dt, at + 32 + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
                                          kk > 0 ? 1u : 0u);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)     // T_hi x [F_hi | F_lo]: steps 0-1 on top, 2-3 in the second
-                    tc_mma_tf32_ts_elect(dt + (kk >> 1) * 64, at + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024),
-                                         kIdesc, kk == 2 ? 0u : 1u);
+                for (int kk = 0; kk < 4; ++kk)     // T_hi x [F_hi | F_lo] on top
+                    tc_mma_tf32_ts_elect(dt, at + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc, 1u);
                 tc_commit_elect(&aempty[a]);
                 tc_commit_elect(&bempty[bs]);
                 tc_commit_elect(&tfull[d]);
@@ -1031,7 +1020,7 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
             if (ok) {
                 tc_fence_after();
                 float yc[RPH];
-                read_acc2<RPH>(tmem_row, d * kTfAccCols, yc);
+                read_rows<RPH>(tmem_row, d * kTfAccCols, yc);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[d]);
@@ -1279,9 +1268,8 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_last(const __grid_consta
                 tc_mma_tf32_ts_elect(dt, at + 32 + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
                                      kk > 0 ? 1u : 0u);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)     // T_hi^T x [F_hi | F_lo]: steps 0-1 on top, 2-3 in the second
-                tc_mma_tf32_ts_elect(dt + (kk >> 1) * 64, at + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
-                                     kk == 2 ? 0u : 1u);
+            for (int kk = 0; kk < 4; ++kk)     // T_hi^T x [F_hi | F_lo] on top
+                tc_mma_tf32_ts_elect(dt, at + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc, 1u);
             tc_commit_elect(&aempty[a]);
             tc_commit_elect(&bempty[bs]);
             tc_commit_elect(&tfull[d]);
@@ -1321,7 +1309,7 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_last(const __grid_consta
         }
         tc_fence_after();
         float y[RPH];
-        read_acc2<RPH>(tmem_row, d * kTfAccCols, y);
+        read_rows<RPH>(tmem_row, d * kTfAccCols, y);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[d]);

@@ -97,10 +97,10 @@ def test_mttkrp_rejects_bad_arguments():
 
 
 def test_fp32_tensor_core_mttkrp_is_unbiased():
-    # The 3xTF32 kernels sum each chunk in three tensor-core accumulators so that few adds
-    # go into a large running sum (each such add drops about half a unit toward zero).  The
-    # mean relative deviation from the oracle stays below 1.5e-7 (one accumulator per chunk
-    # gave -2.3e-7 in every mode; the FFMA kernels give about 1e-9).
+    # The tensor core's FP32 accumulation drops about half a unit toward zero when it adds
+    # into a large running sum.  The 3xTF32 kernels take each chunk's T_lo steps first, while
+    # the sum is small, and keep the mean relative deviation from the oracle near -1e-7 and
+    # below 1.5e-7 (T_hi's steps first gave -2.3e-7 in every mode; FFMA about 1e-9).
     import torch
     import paper_2001_04321_gb300 as ntf
     dims, r = (64, 128, 64), 16
