@@ -171,10 +171,14 @@ NTF_API size_t ntf_mttkrp_workspace_bytes(const ntf_tensor* T, int rank, int mod
  *   out(j,p) = sum over entries with i_mode = j of T[i] * prod_{l != mode} A_l(i_l, p),
  * i.e. T_[n] B^n of Sec. 2 (def:B, def:grad; the N MTTKRPs per iteration that
  * dominate the run time, Sec. 4.1 footnote).  The Khatri-Rao matrix is never
- * formed: the tensor is streamed once (TMA tiles of 128 rows x 64 columns of
- * the last mode), contracted with the last-mode factor, and the remaining
- * factors enter as per-row weights.  Accumulation in FP32 with a fixed
- * reduction order (bitwise reproducible).
+ * formed: the tensor is streamed once in TMA tiles, contracted with one factor,
+ * and the remaining factors enter as per-row weights.  Accumulation in FP32
+ * with a fixed reduction order (bitwise reproducible).  Kernels: for rank <= 32
+ * the tensor cores (BF16 tensors: bf16 MMAs against the factor split into bf16
+ * hi | lo; FP32 tensors: 3xTF32, both operands split into TF32 hi | lo), else
+ * FP32 FMAs.  The environment variable NTF_TF32, read once per process, selects
+ * the FP32 kernels: unset or 1 = tensor cores for every mode, 2 = for the modes
+ * before the last only, 0 = FMAs.
  *   factors: HOST array of `order` device pointers (factors[mode] is unused).
  *   workspace: device buffer of ws_bytes >= ntf_mttkrp_workspace_bytes(), 256-byte aligned.
  * Errors: NTF_EINVAL for bad shape/rank/mode, NULL pointers, misaligned data
