@@ -586,7 +586,7 @@ constexpr int kResRowsPerWarp = 4;
 constexpr int kResGroups = 2;                                    // row groups per warp per chunk
 constexpr int kResRows = (kStreamRedThreads / 32) * kResRowsPerWarp * kResGroups;   // 64 rows per block
 
-int residual_chunk(int r) { return r <= 16 ? 512 : r <= 32 ? 256 : 128; }   // r * CW * 4 <= 32 KB
+int residual_chunk(int r) { return r <= 16 ? 512 : r <= 32 ? 256 : 128; }   // r * (CW + 4) * 4 <= 34 KB
 
 template <typename TE>
 __device__ __forceinline__ void load4(const TE* p, float* x);
@@ -604,27 +604,34 @@ __device__ __forceinline__ void load4<__nv_bfloat16>(const __nv_bfloat16* p, flo
 
 template <typename TE>
 __global__ void __launch_bounds__(kStreamRedThreads) k_residual_sq(const TE* __restrict__ T, int64_t Ii, int64_t n_o,
-                                                                   int64_t C, int64_t ld, int r, int CW,
+                                                                   int64_t C, int64_t ld, int r, int CW, int per,
                                                                    const float* __restrict__ W, int RP,
                                                                    const float* __restrict__ Ai,
                                                                    const float* __restrict__ Ac,
                                                                    double* __restrict__ parts) {
-    extern __shared__ __align__(16) float AcT[];                 // [r][CW]
+    // Work units: (column chunk, row slice), `per` row slices per chunk.  A block stages its
+    // unit's chunk of A_{N-1}^T in shared memory once (coalesced) and streams the slice's rows
+    // (64-row blocks slice, slice + per, ...) against it.  With gridDim.x = units, as the host
+    // arranges whenever it can, every block has one unit.
+    extern __shared__ __align__(16) float AcT[];                 // [r][CW + 4]
     __shared__ __align__(16) float krT[kStreamRedThreads / 32][NTF_MAX_RANK][kResRowsPerWarp];
     __shared__ double sbuf[33];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int CWP = CW + 4;                                       // row pitch: float4-aligned, fewer conflicts
     const int64_t rows = Ii * n_o;
     const int64_t nblk = (rows + kResRows - 1) / kResRows;
+    const int64_t n_chunks = (C + CW - 1) / CW;
     double acc = 0.0;
-    for (int64_t blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-        for (int64_t cb = 0; cb < C; cb += CW) {
-            const int cw = (int)min((int64_t)CW, C - cb);
-            __syncthreads();
-            for (int q = threadIdx.x; q < r * CW; q += blockDim.x) {
-                const int p = q / CW, c = q - p * CW;
-                AcT[q] = c < cw ? Ac[(cb + c) * r + p] : 0.f;
-            }
-            __syncthreads();
+    for (int64_t u = blockIdx.x; u < n_chunks * per; u += gridDim.x) {
+        const int64_t cb = (u / per) * CW;
+        const int cw = (int)min((int64_t)CW, C - cb);
+        __syncthreads();
+        for (int q = threadIdx.x; q < r * CW; q += blockDim.x) {
+            const int c = q / r, p = q - c * r;                   // consecutive q: consecutive A_{N-1} entries
+            AcT[p * CWP + c] = c < cw ? Ac[(cb + c) * r + p] : 0.f;
+        }
+        __syncthreads();
+        for (int64_t blk = u % per; blk < nblk; blk += per) {
             for (int g = 0; g < kResGroups; ++g) {
                 const int64_t row0 = blk * kResRows + (int64_t)(g * (kStreamRedThreads / 32) + wl) * kResRowsPerWarp;
                 if (row0 >= rows) continue;                        // warp-uniform
@@ -652,7 +659,7 @@ __global__ void __launch_bounds__(kStreamRedThreads) k_residual_sq(const TE* __r
 #pragma unroll
                     for (int k = 0; k < kResRowsPerWarp; ++k) x[k][0] = x[k][1] = x[k][2] = x[k][3] = 0.f;
                     for (int p = 0; p < r; ++p) {
-                        const float4 a = *reinterpret_cast<const float4*>(&AcT[p * CW + c0]);
+                        const float4 a = *reinterpret_cast<const float4*>(&AcT[p * CWP + c0]);
                         const float4 kk = *reinterpret_cast<const float4*>(&krT[wl][p][0]);
                         const float kv[4] = {kk.x, kk.y, kk.z, kk.w};
 #pragma unroll
@@ -683,15 +690,19 @@ __global__ void __launch_bounds__(kStreamRedThreads) k_residual_sq(const TE* __r
 cudaError_t launch_residual_sq(const TensorView& v, int r, const float* W, int RP, const float* Ai, const float* Ac,
                                double* parts, double* out, cudaStream_t st) {
     const int64_t nblk = (v.Ii * v.n_o + kResRows - 1) / kResRows;
-    const int G = (int)std::min<int64_t>(nblk, stream_red_blocks());
     const int CW = residual_chunk(r);
-    const size_t smem = sizeof(float) * (size_t)r * CW;
+    const int64_t n_chunks = (v.C + CW - 1) / CW;
+    // row slices per column chunk; one block per (chunk, slice) unit while they fit in the
+    // partial-sum buffer (stream_red_blocks() entries), else blocks loop over units
+    const int64_t per = std::max<int64_t>(1, std::min<int64_t>(nblk, stream_red_blocks() / n_chunks));
+    const int G = (int)std::min<int64_t>(per * n_chunks, stream_red_blocks());
+    const size_t smem = sizeof(float) * (size_t)r * (CW + 4);
     if (v.dtype == NTF_F32)
         k_residual_sq<float><<<G, kStreamRedThreads, smem, st>>>(static_cast<const float*>(v.data), v.Ii, v.n_o, v.C,
-                                                                 v.ld, r, CW, W, RP, Ai, Ac, parts);
+                                                                 v.ld, r, CW, (int)per, W, RP, Ai, Ac, parts);
     else
         k_residual_sq<__nv_bfloat16><<<G, kStreamRedThreads, smem, st>>>(
-            static_cast<const __nv_bfloat16*>(v.data), v.Ii, v.n_o, v.C, v.ld, r, CW, W, RP, Ai, Ac, parts);
+            static_cast<const __nv_bfloat16*>(v.data), v.Ii, v.n_o, v.C, v.ld, r, CW, (int)per, W, RP, Ai, Ac, parts);
     count_launch();
     k_sum_parts<<<1, 256, 0, st>>>(parts, G, out);
     count_launch();
