@@ -449,6 +449,7 @@ ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* wor
             T.w_sel = fused->w_sel;
             T.w_flip = fused->w_flip;
             T.job = fused->job;
+            T.early = fused->early;
         }
         grid = P.kind == ModeKind::Last ? dim3(P.G, P.n_cb, 1) : dim3(P.G, 1, 1);
         smem = P.tf32 ? tf32_rows_smem(P.RPH) : P.kind == ModeKind::Last ? tc_last_smem(P.RPH) : tc_rows_smem(P.RPH);

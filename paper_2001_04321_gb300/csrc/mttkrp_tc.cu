@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
             }
         }
     }
-    pdl_wait();
+    if (!P.early || warp < 4) pdl_wait();
     pdl_trigger();
 
     if (warp == 4) {

@@ -31,6 +31,10 @@ struct TcParams {
     const float* Wb[2];             // W = Wb[cur[w_sel] ^ w_flip]
     int fct_sel, fi_sel, fi_flip, w_sel, w_flip;
     GramJob job;                    // Grams + V for the epilogue after this stream (job.rr == 0: none)
+    // rows kernels: the producer and MMA warps read nothing the kernel before this one writes
+    // (its operands and tile counter were written two or more kernels back), so only the
+    // epilogue warps wait for it and the tensor streams in while it finishes
+    int early;
 };
 
 size_t tc_rows_smem(int rph);

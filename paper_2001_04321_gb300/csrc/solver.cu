@@ -248,6 +248,10 @@ struct Solver {
         T.Wb[1] = X[0][1];
         T.w_sel = 0;
         T.w_flip = (use_her && n > 0) ? 1 : 0;
+        // mode 1's packed operand and buffer index come from the previous iteration's last
+        // epilogue and its tile counter from that epilogue too: its tensor can stream in
+        // while the mode-0 epilogue runs
+        T.early = n == 1 ? 1 : 0;
         GramJob& J = T.job;
         J.rr = r * r;
         J.order = N;
@@ -289,7 +293,9 @@ struct Solver {
             if (s != NTF_OK) return s;
             EpiParams ep = make_epi(n);
             if (direct) {
-                const int nx = (n + 1) % N;
+                // the tile counter of the stream after next (two kernels before its launch, so
+                // that an early stream does not depend on the epilogue right before it)
+                const int nx = (n + 2) % N;
                 const MttkrpPlan& Q = plan[nx];
                 ep.sched_next = Q.tile_slots ? reinterpret_cast<unsigned int*>(wsm[nx] + Q.off_sched) : nullptr;
                 ep.v_from_stream = 1;
@@ -511,6 +517,11 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
             }
             if ((s = S->alloc((void**)&S->packLast, last_b)) != NTF_OK) return bail(s);
             NTF_CUDA_TRY(cudaMemsetAsync(S->packLast, 0, last_b, st));
+            // every epilogue resets the counter of the stream two launches ahead; the first
+            // iteration's streams start from these
+            for (int n = 0; n < N; ++n)
+                if (S->plan[n].tile_slots)
+                    NTF_CUDA_TRY(cudaMemsetAsync(S->wsm[n] + S->plan[n].off_sched, 0, sizeof(unsigned int), st));
         }
     }
     S->ws_res_bytes = (((sizeof(float) * (size_t)S->vu.n_o * round_up(r, 4)) + 255) & ~size_t(255)) +
