@@ -36,6 +36,36 @@ constexpr int kEpiWarps = 8;
 constexpr int kEpiRows = 4;                              // rows per CTA
 constexpr int kEpiPieces = kEpiWarps / kEpiRows;         // partial-sum pieces per output
 
+// Element (row i, column nn of 2 RPH) of the 3xTF32 operand: 32-row chunks of 2 RPH rows x
+// 128 B, 16-byte groups swizzled as a 128-byte-swizzled TMA box; columns [0, RPH) hold tf32(x),
+// [RPH, 2 RPH) hold tf32(x - tf32(x)).  (FP32 word index.)
+__device__ __forceinline__ int64_t packed_index_tf32(int64_t i, int nn, int rph) {
+    const int N = 2 * rph;
+    const int64_t kc = i >> 5;
+    const int kl = (int)(i & 31);
+    return ((kc * N + nn) * 128 + (((kl >> 2) ^ (nn & 7)) << 4) + (kl & 3) * 4) / 4;
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    return __uint_as_float(h);
+}
+
+// write row `row`, column `lane` of the next stream's operand (bf16 hi | lo or TF32 hi | lo)
+__device__ __forceinline__ void pack_store(__nv_bfloat16* dst, int64_t row, int lane, int rph, int tf32, float x) {
+    if (tf32) {
+        float* f = reinterpret_cast<float*>(dst);
+        const float hi = tf32_rna(x);
+        f[packed_index_tf32(row, lane, rph)] = hi;
+        f[packed_index_tf32(row, rph + lane, rph)] = tf32_rna(x - hi);
+    } else {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        dst[packed_index(row, lane, rph)] = hi;
+        dst[packed_index(row, rph + lane, rph)] = __float2bfloat16_rn(x - __bfloat162float(hi));
+    }
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -309,19 +339,11 @@ __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) 
                 Ah[row * r + lane] = ah;
             }
             inner = m * a;
-            // the next stream's tensor-core operand: bf16 hi | lo of this row
+            // the next stream's tensor-core operand: hi | lo of this row
             __nv_bfloat16* pa = P.packA[cn];
             __nv_bfloat16* ph = her ? P.packH[1 - cn] : nullptr;
-            if (pa) {
-                const __nv_bfloat16 hi = __float2bfloat16_rn(a);
-                pa[packed_index(row, lane, P.pack_rph)] = hi;
-                pa[packed_index(row, P.pack_rph + lane, P.pack_rph)] = __float2bfloat16_rn(a - __bfloat162float(hi));
-            }
-            if (ph) {
-                const __nv_bfloat16 hi = __float2bfloat16_rn(ah);
-                ph[packed_index(row, lane, P.pack_rph)] = hi;
-                ph[packed_index(row, P.pack_rph + lane, P.pack_rph)] = __float2bfloat16_rn(ah - __bfloat162float(hi));
-            }
+            if (pa) pack_store(pa, row, lane, P.pack_rph, P.pack_tf32, a);
+            if (ph) pack_store(ph, row, lane, P.pack_rph, P.pack_tf32, ah);
         }
         rowsA[rw][lane] = live ? a : 0.f;
         rowsH[rw][lane] = live ? ah : 0.f;

@@ -68,6 +68,7 @@ struct EpiParams {
     __nv_bfloat16* packA[2];   // A_k's rows go to packA[cur] (if set), in the tensor-core layout
     __nv_bfloat16* packH[2];   // A_hat_k's rows go to packH[1 - cur] (if set)
     int pack_rph;
+    int pack_tf32;             // the 3xTF32 layout (FP32 words, 32-row chunks) instead of bf16 hi | lo
     unsigned int* sched_next;  // run-time tile counter of the next stream, set to 0 here (or nullptr)
     int v_from_stream;         // V is formed by the preceding stream (read after the wait)
 };

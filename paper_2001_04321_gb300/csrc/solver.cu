@@ -304,11 +304,13 @@ struct Solver {
                     ep.packA[0] = ep.packH[0] = packRows[0];
                     ep.packA[1] = ep.packH[1] = packRows[1];
                     ep.pack_rph = plan[0].RPH;
+                    ep.pack_tf32 = plan[0].tf32 ? 1 : 0;
                 } else if (n == N - 2) {
                     // the last-mode stream reads the pairing factor of mode N-2
                     if (use_her) ep.packH[0] = ep.packH[1] = packLast;
                     else ep.packA[0] = ep.packA[1] = packLast;
                     ep.pack_rph = plan[N - 1].RPH;
+                    ep.pack_tf32 = plan[N - 1].tf32 ? 1 : 0;
                 }
             }
             cudaError_t e = launch_epilogue(ep, st, pdl && !timer);
@@ -505,12 +507,14 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
         if ((s = S->alloc((void**)&S->gpart, sizeof(float) * (size_t)blocks * 2 * r * r)) != NTF_OK) return bail(s);
         if ((s = S->alloc((void**)&S->ipart, sizeof(double) * (size_t)blocks)) != NTF_OK) return bail(s);
         if ((s = S->alloc((void**)&S->qpart, sizeof(double) * (size_t)blocks)) != NTF_OK) return bail(s);
-        // (the epilogues write the packed bf16 operand layout, so not with the TF32 kernels)
-        S->direct = N == 3 && S->plan[0].tc && S->plan[1].tc && S->plan[2].tc && !S->plan[0].tf32;
+        // every mode on the tensor cores, all BF16 or all 3xTF32 (the epilogues write one layout)
+        S->direct = N == 3 && S->plan[0].tc && S->plan[1].tc && S->plan[2].tc &&
+                    S->plan[0].tf32 == S->plan[2].tf32;
         if (S->direct) {
             // packed operands, zero outside the factor rows and columns
             const size_t rows_b = (size_t)S->plan[0].n_kc * 2 * S->plan[0].RPH * 128;
-            const size_t last_b = (size_t)S->plan[2].nb * tc_last_b_bytes(S->plan[2].RPH);
+            const size_t last_b = (size_t)S->plan[2].nb *
+                                  (S->plan[2].tf32 ? (size_t)(2 * S->plan[2].RPH) * 128 : tc_last_b_bytes(S->plan[2].RPH));
             for (int k = 0; k < 2; ++k) {
                 if ((s = S->alloc((void**)&S->packRows[k], rows_b)) != NTF_OK) return bail(s);
                 NTF_CUDA_TRY(cudaMemsetAsync(S->packRows[k], 0, rows_b, st));

@@ -185,7 +185,8 @@ def test_prepared_graph_with_timing_matches_eager():
         before = ntf.launch_count()
         s2.run(5)
         ms, n, nbytes = s2.mttkrp_time()
-        assert ntf.launch_count() - before >= 5 * 3 * 3
+        # 3-way tensor-core path: a stream and an epilogue per mode, 6 launches per iteration
+        assert ntf.launch_count() - before >= 5 * 3 * 2
         s2.get_factors(F2)
         st.synchronize()
     assert n == 15 and ms > 0 and nbytes == T.size * 4
