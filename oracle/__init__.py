@@ -60,15 +60,23 @@ def _load():
             lib.oracle_objective_identity.restype = C.c_double
             lib.oracle_hals.argtypes = [_D, C.c_int64, C.c_int, _D, _D, C.c_int, C.c_double]
             lib.oracle_pgd.argtypes = lib.oracle_hals.argtypes
+            lib.oracle_nesterov.argtypes = lib.oracle_hals.argtypes
             lib.oracle_lambda_max.argtypes = [_D, C.c_int]
             lib.oracle_lambda_max.restype = C.c_double
             lib.oracle_extrapolate.argtypes = [_D, _D, C.c_double, C.c_int64, _D]
             lib.oracle_extrapolate.restype = None
             lib.oracle_her_decide.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double]
-            lib.oracle_solve.argtypes = [C.c_int, _I64, _D, C.POINTER(_D), C.c_int,
-                                         C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
-                                         C.c_double, C.c_double, C.c_double, C.c_double,
-                                         _D, _D, _D, C.POINTER(C.c_int), _D, _D, _D]
+            tail = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                    C.c_double, C.c_double, C.c_double, C.c_double,
+                    _D, _D, _D, C.POINTER(C.c_int), _D, _D, _D, _D]
+            lib.oracle_solve.argtypes = [C.c_int, _I64, _D, C.POINTER(_D), C.c_int] + tail
+            lib.oracle_solve_tucker.argtypes = [C.c_int, _I64, _I64, _D, C.POINTER(_D), C.POINTER(_D),
+                                                C.c_int] + tail
+            lib.oracle_tucker_expand.argtypes = [C.c_int, _I64, _I64, _D, C.POINTER(_D), _D]
+            lib.oracle_tucker_mttkrp.argtypes = [C.c_int, _I64, _I64, _D, C.POINTER(_D), C.POINTER(_D),
+                                                 C.c_int, C.c_int, _D]
+            lib.oracle_tucker_norm_sq.argtypes = [C.c_int, _I64, _I64, _D, C.POINTER(_D)]
+            lib.oracle_tucker_norm_sq.restype = C.c_double
             lib.oracle_round_bf16.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_uint16), C.c_int64]
             lib.oracle_round_bf16.restype = None
             _lib = lib
@@ -200,6 +208,16 @@ def pgd(A, M, V, inner_max: int = 1, inner_tol: float = 1e-2):
     return A, s
 
 
+def nesterov(A, M, V, inner_max: int = 1, inner_tol: float = 1e-2):
+    """AO-Nesterov block update (Sec. 2.1; momentum sequence t_k of Appendix B,
+    projected gradient step of eq. projgrad) on a copy of ``A``; returns (A_new, steps)."""
+    A = _f64(A).copy()
+    M = _f64(M)
+    V = _f64(V)
+    s = _load().oracle_nesterov(_ptr(A), A.shape[0], A.shape[1], _ptr(M), _ptr(V), inner_max, inner_tol)
+    return A, s
+
+
 def lambda_max(V) -> float:
     """Largest eigenvalue of a symmetric matrix by cyclic Jacobi rotations."""
     V = _f64(V)
@@ -240,7 +258,10 @@ def bf16_to_f64(bits) -> np.ndarray:
 
 
 class SolveTrace:
-    def __init__(self, iters: int, order: int):
+    def __init__(self, iters: int, dims, r: int, track_factors: bool):
+        order = len(dims)
+        self.dims = [int(d) for d in dims]
+        self.r = r
         self.fhat = np.zeros(iters)
         self.beta = np.zeros(iters)
         self.beta_bar = np.zeros(iters)
@@ -248,31 +269,123 @@ class SolveTrace:
         self.ftrue = np.zeros(iters)
         self.fblock = np.zeros(iters * order)
         self.fhat0 = np.zeros(1)
+        S = sum(self.dims) * r
+        self._fac = np.zeros(iters * 3 * S) if track_factors else None
+
+    def _factors(self, k: int, which: int):
+        S = sum(self.dims) * self.r
+        flat = self._fac[(k - 1) * 3 * S + which * S:(k - 1) * 3 * S + (which + 1) * S]
+        out, o = [], 0
+        for d in self.dims:
+            out.append(flat[o:o + d * self.r].reshape(d, self.r))
+            o += d * self.r
+        return out
+
+    def A_updated(self, k: int):
+        """Factors A^l_k right after the block updates of iteration k (1-based)."""
+        return self._factors(k, 0)
+
+    def A_hat(self, k: int):
+        """Extrapolated factors A_hat^l_k of iteration k before the restart decision."""
+        return self._factors(k, 1)
+
+    def A_after(self, k: int):
+        """Factors A^l_k after iteration k's restart decision."""
+        return self._factors(k, 2)
+
+
+_METHODS = {"hals": 0, "pgd": 1, "nesterov": 2}
+
+
+def _solve_common(fn, prefix, dims, init, iters, her, method, inner_max, inner_tol, beta0, gamma,
+                  gamma_bar, eta, track_true, track_blocks, track_factors):
+    F = [_f64(A).copy() for A in init]
+    r = F[0].shape[1]
+    tr = SolveTrace(iters, dims, r, track_factors)
+    rc = fn(*prefix, _ptr_array(F), r, int(her), _METHODS[method], inner_max, inner_tol, iters,
+            beta0, gamma, gamma_bar, eta,
+            _ptr(tr.fhat), _ptr(tr.beta), _ptr(tr.beta_bar),
+            tr.restart.ctypes.data_as(C.POINTER(C.c_int)),
+            _ptr(tr.ftrue) if track_true else None,
+            _ptr(tr.fblock) if track_blocks else None,
+            _ptr(tr.fhat0),
+            _ptr(tr._fac) if track_factors else None)
+    if rc:
+        raise ValueError("oracle solve: bad arguments")
+    return F, tr
 
 
 def solve(T, init, iters: int, her: bool = True, method: str = "hals", inner_max: int = 1,
           inner_tol: float = 1e-2, beta0: float = 0.5, gamma: float = 1.05,
           gamma_bar: float = 1.01, eta: float = 1.5, track_true: bool = False,
-          track_blocks: bool = False):
+          track_blocks: bool = False, track_factors: bool = False):
     """Alg. 1 (``her=False``) or Alg. 2 (``her=True``) in FP64 from ``init``.
+    ``method`` is "hals", "pgd" or "nesterov".
 
     Returns ``(factors, trace)``; ``trace.fhat[k-1]`` is F-hat_k (the value Alg. 2's restart test compares),
-    ``trace.ftrue[k-1]`` the explicit objective at A_k when ``track_true``.
+    ``trace.ftrue[k-1]`` the explicit objective at A_k when ``track_true``; with ``track_factors``
+    the trace also holds every iteration's factors (``A_updated``, ``A_hat``, ``A_after``).
     """
     lib = _load()
     T = _f64(T)
-    F = [_f64(A).copy() for A in init]
-    r = F[0].shape[1]
     d, dp = _dims(T)
-    tr = SolveTrace(iters, T.ndim)
-    rc = lib.oracle_solve(T.ndim, dp, _ptr(T), _ptr_array(F), r, int(her),
-                          0 if method == "hals" else 1, inner_max, inner_tol, iters,
-                          beta0, gamma, gamma_bar, eta,
-                          _ptr(tr.fhat), _ptr(tr.beta), _ptr(tr.beta_bar),
-                          tr.restart.ctypes.data_as(C.POINTER(C.c_int)),
-                          _ptr(tr.ftrue) if track_true else None,
-                          _ptr(tr.fblock) if track_blocks else None,
-                          _ptr(tr.fhat0))
+    return _solve_common(lib.oracle_solve, (T.ndim, dp, _ptr(T)), T.shape, init, iters, her, method,
+                         inner_max, inner_tol, beta0, gamma, gamma_bar, eta, track_true, track_blocks,
+                         track_factors)
+
+
+# --- Tucker-format data (Appendix A) -----------------------------------------
+
+def _tucker_args(G, U):
+    G = _f64(G)
+    U = [_f64(u) for u in U]
+    dims = np.asarray([u.shape[0] for u in U], dtype=np.int64)
+    cdims = np.asarray(G.shape, dtype=np.int64)
+    if len(U) != G.ndim or any(u.shape[1] != c for u, c in zip(U, G.shape)):
+        raise ValueError("U_p must be dims[p] x G.shape[p]")
+    return G, U, dims, cdims
+
+
+def tucker_expand(G, U) -> np.ndarray:
+    """The tensor ``(U_0 (x) ... (x) U_{N-1}) G`` written out entry by entry (tiny inputs)."""
+    G, U, dims, cdims = _tucker_args(G, U)
+    T = np.zeros(tuple(int(x) for x in dims))
+    rc = _load().oracle_tucker_expand(G.ndim, dims.ctypes.data_as(_I64), cdims.ctypes.data_as(_I64), _ptr(G),
+                                      _ptr_array(U), _ptr(T))
     if rc:
-        raise ValueError("oracle_solve: bad arguments")
-    return F, tr
+        raise ValueError("oracle_tucker_expand: bad arguments")
+    return T
+
+
+def tucker_mttkrp(G, U, factors, mode: int) -> np.ndarray:
+    """MTTKRP of the Tucker-format tensor through its core (Appendix A):
+    ``U_n MTTKRP(G, {U_p^T A_p}, n)``."""
+    G, U, dims, cdims = _tucker_args(G, U)
+    F = [_f64(A) for A in factors]          # factors[mode] is not read
+    r = F[0 if mode != 0 else 1].shape[1]
+    M = np.zeros((int(dims[mode]), r))
+    rc = _load().oracle_tucker_mttkrp(G.ndim, dims.ctypes.data_as(_I64), cdims.ctypes.data_as(_I64), _ptr(G),
+                                      _ptr_array(U), _ptr_array(F), r, mode, _ptr(M))
+    if rc:
+        raise ValueError("oracle_tucker_mttkrp: bad arguments")
+    return M
+
+
+def tucker_norm_sq(G, U) -> float:
+    """``||(U_0 (x) ... (x) U_{N-1}) G||_F^2`` through the core and the Grams of U_p."""
+    G, U, dims, cdims = _tucker_args(G, U)
+    return float(_load().oracle_tucker_norm_sq(G.ndim, dims.ctypes.data_as(_I64), cdims.ctypes.data_as(_I64),
+                                               _ptr(G), _ptr_array(U)))
+
+
+def solve_tucker(G, U, init, iters: int, her: bool = True, method: str = "hals", inner_max: int = 1,
+                 inner_tol: float = 1e-2, beta0: float = 0.5, gamma: float = 1.05,
+                 gamma_bar: float = 1.01, eta: float = 1.5, track_true: bool = False,
+                 track_blocks: bool = False, track_factors: bool = False):
+    """Alg. 1 / Alg. 2 on the Tucker-format objective F_t of Appendix A (eq. objFunTucker)."""
+    lib = _load()
+    G, U, dims, cdims = _tucker_args(G, U)
+    return _solve_common(lib.oracle_solve_tucker,
+                         (G.ndim, dims.ctypes.data_as(_I64), cdims.ctypes.data_as(_I64), _ptr(G), _ptr_array(U)),
+                         [int(x) for x in dims], init, iters, her, method, inner_max, inner_tol, beta0, gamma,
+                         gamma_bar, eta, track_true, track_blocks, track_factors)

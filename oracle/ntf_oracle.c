@@ -10,7 +10,7 @@
  * header, table or helper with the CUDA library; both receive the same seeded
  * inputs from the generator module and nothing else.
  *
- * Conventions (the paper leaves them open):
+ * Conventions (the paper leaves them open; the CUDA path adopts the same):
  *   - a tensor of order N with dims I_0..I_{N-1} is stored C-order (last mode
  *     fastest); modes are 0-based here (the paper's mode i is our mode i-1);
  *   - a factor A_l is row-major I_l x r (r contiguous);
@@ -24,7 +24,9 @@
  *
  * Parity status per function (what pins it is in tests/test_oracle_*.py):
  *   mttkrp, mttkrp_kr, gram, hadamard_grams, objective_*, hals, pgd,
- *   lambda_max, extrapolate, her_decide, solve, round_bf16: pinned.
+ *   nesterov, lambda_max, extrapolate, her_decide, solve (including how
+ *   Alg. 2 composes its steps), tucker_expand, tucker_mttkrp,
+ *   tucker_norm_sq, solve_tucker, round_bf16: pinned.
  */
 #include <math.h>
 #include <stdint.h>
@@ -392,36 +394,235 @@ int oracle_her_decide(double* state, double f_hat, double gamma, double gamma_ba
     return restart;
 }
 
+/* AO-Nesterov block update (Sec. 2.1, "AO-Nesterov": Nesterov's accelerated
+ * gradient method on the block NNLS).  The paper names the method without
+ * writing it out; this follows the two ingredients it does print: the
+ * projected gradient step with step 1/L of eq. projgrad (L = lambda_max(V),
+ * Sec. 2.2) and the momentum sequence t_k of Appendix B (t_0 = 1,
+ * t_s = (1 + sqrt(1 + 4 t_{s-1}^2)) / 2, weight (t_{s-1} - 1) / t_s).
+ * With X_0 = Y_0 = A:
+ *   X_s = max(0, Y_{s-1} - (Y_{s-1} V - M) / L),
+ *   Y_s = X_s + w_s (X_s - X_{s-1}),   w_s = (t_{s-1} - 1) / t_s,
+ * under the inner stopping rule of Sec. 4.1 applied to ||X_s - X_{s-1}||.
+ * A receives the last X_s.  Returns the number of steps. */
+int oracle_nesterov(double* A, int64_t rows, int r, const double* M, const double* V,
+                    int inner_max, double inner_tol) {
+    const int64_t n = rows * r;
+    const double L = oracle_lambda_max(V, r);
+    double* prev = (double*)malloc(sizeof(double) * (size_t)n);
+    double* Y = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!prev || !Y) { free(prev); free(Y); return -2; }
+    if (!(L > 0.0)) { free(prev); free(Y); return 0; }
+    memcpy(Y, A, sizeof(double) * (size_t)n);               /* Y_0 = X_0 */
+    double t = 1.0;                                          /* t_0 */
+    double delta_1 = 0.0;
+    int s = 0;
+    for (;;) {
+        ++s;
+        memcpy(prev, A, sizeof(double) * (size_t)n);         /* X_{s-1} */
+        for (int64_t i = 0; i < rows; ++i)
+            for (int j = 0; j < r; ++j) {
+                double g = -M[i * r + j];
+                for (int l = 0; l < r; ++l) g += Y[i * r + l] * V[l * r + j];
+                const double v = Y[i * r + j] - g / L;
+                A[i * r + j] = v > 0.0 ? v : 0.0;            /* X_s */
+            }
+        const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        const double w = (t - 1.0) / t_next;
+        t = t_next;
+        for (int64_t i = 0; i < n; ++i) Y[i] = A[i] + w * (A[i] - prev[i]);
+        const double delta = frob_diff(A, prev, n);
+        if (s == 1) delta_1 = delta;
+        if (inner_stop(s, delta, delta_1, inner_max, inner_tol)) break;
+    }
+    free(prev);
+    free(Y);
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tucker-format data (Appendix A)                                           */
+/* ------------------------------------------------------------------------ */
+
+/* The tensor (U_0 (x) ... (x) U_{N-1}) G of Appendix A written out entry by
+ * entry: T[i] = sum over core entries q of G[q] prod_p U_p(i_p, q_p).  U_p is
+ * row-major dims[p] x cdims[p]; G is C-order with dims cdims.  Tiny inputs. */
+int oracle_tucker_expand(int order, const int64_t* dims, const int64_t* cdims, const double* G,
+                         const double* const* U, double* T) {
+    if (check_shape(order, dims, 1) || check_shape(order, cdims, 1)) return -1;
+    const int64_t total = numel_of(order, dims);
+    const int64_t ctotal = numel_of(order, cdims);
+    int64_t idx[MAXORD] = {0};
+    for (int64_t lin = 0; lin < total; ++lin) {
+        int64_t q[MAXORD] = {0};
+        double s = 0.0;
+        for (int64_t c = 0; c < ctotal; ++c) {
+            double prod = G[c];
+            for (int p = 0; p < order; ++p) prod *= U[p][idx[p] * cdims[p] + q[p]];
+            s += prod;
+            odometer_next(order, cdims, q);
+        }
+        T[lin] = s;
+        odometer_next(order, dims, idx);
+    }
+    return 0;
+}
+
+/* MTTKRP of the Tucker-format tensor, by the route of the gradient formula of
+ * Appendix A: with W_p = U_p^T A_p (cdims[p] x r),
+ *   M_n = U_n * MTTKRP(G, {W_p}_{p != n}, n),
+ * which equals the MTTKRP of the expanded tensor because the unfolding of
+ * (U_0 (x) ... (x) U_{N-1}) G is U_n G_[n] (Kronecker of the other U_p)^T and
+ * (Kronecker of U_p)^T (Khatri-Rao of A_p) = Khatri-Rao of U_p^T A_p.  Only
+ * products of the sizes of U_p, A_p and G appear. */
+int oracle_tucker_mttkrp(int order, const int64_t* dims, const int64_t* cdims, const double* G,
+                         const double* const* U, const double* const* A, int r, int n, double* M) {
+    if (check_shape(order, dims, r) || check_shape(order, cdims, r) || n < 0 || n >= order) return -1;
+    double* W[MAXORD] = {0};
+    double* Y = (double*)malloc(sizeof(double) * (size_t)cdims[n] * (size_t)r);
+    int rc = Y ? 0 : -2;
+    for (int p = 0; p < order && rc == 0; ++p) {
+        if (p == n) continue;
+        W[p] = (double*)malloc(sizeof(double) * (size_t)cdims[p] * (size_t)r);
+        if (!W[p]) { rc = -2; break; }
+        for (int64_t q = 0; q < cdims[p]; ++q)
+            for (int j = 0; j < r; ++j) {
+                double s = 0.0;
+                for (int64_t i = 0; i < dims[p]; ++i) s += U[p][i * cdims[p] + q] * A[p][i * r + j];
+                W[p][q * r + j] = s;
+            }
+    }
+    if (rc == 0) rc = oracle_mttkrp(order, cdims, G, (const double* const*)W, r, n, Y);
+    if (rc == 0)
+        for (int64_t i = 0; i < dims[n]; ++i)
+            for (int j = 0; j < r; ++j) {
+                double s = 0.0;
+                for (int64_t q = 0; q < cdims[n]; ++q) s += U[n][i * cdims[n] + q] * Y[q * r + j];
+                M[i * r + j] = s;
+            }
+    for (int p = 0; p < order; ++p) free(W[p]);
+    free(Y);
+    return rc;
+}
+
+/* ||(U_0 (x) ... (x) U_{N-1}) G||_F^2 without expanding:  <G, G x_0 Q_0 ... x_{N-1} Q_{N-1}>
+ * with Q_p = U_p^T U_p (cdims[p] x cdims[p]); Z x_p Q replaces every mode-p
+ * fibre z of Z by Q z. */
+double oracle_tucker_norm_sq(int order, const int64_t* dims, const int64_t* cdims, const double* G,
+                             const double* const* U) {
+    if (check_shape(order, dims, 1) || check_shape(order, cdims, 1)) return NAN;
+    const int64_t ctotal = numel_of(order, cdims);
+    double* Z = (double*)malloc(sizeof(double) * (size_t)ctotal);
+    double* Z2 = (double*)malloc(sizeof(double) * (size_t)ctotal);
+    if (!Z || !Z2) { free(Z); free(Z2); return NAN; }
+    memcpy(Z, G, sizeof(double) * (size_t)ctotal);
+    for (int p = 0; p < order; ++p) {
+        const int64_t rp = cdims[p];
+        double* Q = (double*)malloc(sizeof(double) * (size_t)rp * (size_t)rp);
+        if (!Q) { free(Z); free(Z2); return NAN; }
+        for (int64_t a = 0; a < rp; ++a)
+            for (int64_t b = 0; b < rp; ++b) {
+                double s = 0.0;
+                for (int64_t i = 0; i < dims[p]; ++i) s += U[p][i * rp + a] * U[p][i * rp + b];
+                Q[a * rp + b] = s;
+            }
+        int64_t stride = 1;                       /* C order: stride of mode p */
+        for (int l = p + 1; l < order; ++l) stride *= cdims[l];
+        int64_t idx[MAXORD] = {0};
+        for (int64_t lin = 0; lin < ctotal; ++lin) {
+            const int64_t base = lin - idx[p] * stride;
+            double s = 0.0;
+            for (int64_t b = 0; b < rp; ++b) s += Q[idx[p] * rp + b] * Z[base + b * stride];
+            Z2[lin] = s;
+            odometer_next(order, cdims, idx);
+        }
+        memcpy(Z, Z2, sizeof(double) * (size_t)ctotal);
+        free(Q);
+    }
+    double s = 0.0;
+    for (int64_t c = 0; c < ctotal; ++c) s += G[c] * Z[c];
+    free(Z);
+    free(Z2);
+    return s;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Solver: Alg. 1 (her = 0) and Alg. 2 (her = 1)                            */
 /* ------------------------------------------------------------------------ */
 
-/* method: 0 = HALS, 1 = projected gradient.
+/* The data term: a dense tensor T, or (Appendix A) a Tucker-format tensor
+ * given by its core G (dims cdims) and factors U_p, never expanded. */
+typedef struct {
+    const double* T;            /* dense tensor, or the core G */
+    const int64_t* cdims;       /* NULL for dense data */
+    const double* const* U;     /* NULL for dense data */
+} data_term;
+
+static int data_mttkrp(const data_term* D, int order, const int64_t* dims, const double* const* A,
+                       int r, int n, double* M) {
+    if (!D->U) return oracle_mttkrp(order, dims, D->T, A, r, n, M);
+    return oracle_tucker_mttkrp(order, dims, D->cdims, D->T, D->U, A, r, n, M);
+}
+
+/* ||T - [[A]]||^2: explicit for dense data; for Tucker data by the identity of
+ * the restart mechanism with a fresh MTTKRP of the last mode (exact up to
+ * rounding, pinned against explicit expansion on tiny inputs). */
+static double data_objective(const data_term* D, int order, const int64_t* dims, double tnorm,
+                             const double* const* A, int r) {
+    if (!D->U) return oracle_objective_explicit(order, dims, D->T, A, r);
+    const int last = order - 1;
+    double* M = (double*)malloc(sizeof(double) * (size_t)dims[last] * (size_t)r);
+    double* V = (double*)malloc(sizeof(double) * (size_t)r * (size_t)r);
+    double* G[MAXORD] = {0};
+    double f = NAN;
+    int ok = M && V;
+    for (int l = 0; l < order && ok; ++l) {
+        G[l] = (double*)malloc(sizeof(double) * (size_t)r * (size_t)r);
+        ok = G[l] != NULL;
+        if (ok) oracle_gram(A[l], dims[l], r, G[l]);
+    }
+    if (ok) {
+        oracle_hadamard_grams((const double* const*)G, order, last, r, V);
+        if (data_mttkrp(D, order, dims, A, r, last, M) == 0)
+            f = oracle_objective_identity(tnorm, M, A[last], dims[last], r, V);
+    }
+    for (int l = 0; l < order; ++l) free(G[l]);
+    free(M);
+    free(V);
+    return f;
+}
+
+/* method: 0 = HALS, 1 = projected gradient, 2 = AO-Nesterov.
  * Outputs (each may be NULL), one entry per outer iteration k = 1..max_iters:
  *   out_fhat[k-1]     F-hat_k = ||T - [[A_hat^1..A_hat^{N-1}, A^N]]||^2 by the
  *                     identity from the last block's MTTKRP (Alg. 2, restart test);
  *   out_beta[k-1], out_beta_bar[k-1], out_restart[k-1]  after the decision;
- *   out_ftrue[k-1]    ||T - [[A_k]]||^2 explicitly (eq. err_true_def, times 2);
- *   out_fblock[(k-1)N + i]  ||T - X||^2 right after block i's update, explicit
+ *   out_ftrue[k-1]    ||T - [[A_k]]||^2 (eq. err_true_def, times 2);
+ *   out_fblock[(k-1)N + i]  ||T - X||^2 right after block i's update
  *                     (pins the monotone decrease of Alg. 1, Sec. 2.1);
- *   out_fhat0         F-hat_0 = ||T - [[A_0]]||^2, explicit.
+ *   out_fhat0         F-hat_0 = ||T - [[A_0]]||^2;
+ *   out_factors       per iteration 3 S values, S = sum_l dims[l] r: the
+ *                     factors A^l_k right after the block updates, the
+ *                     extrapolated A_hat^l_k before the decision, and A^l_k
+ *                     after the decision, each mode after mode.
  * A holds the initial factors on entry and the final A_k on exit. */
-int oracle_solve(int order, const int64_t* dims, const double* T, double* const* A, int r,
-                 int her, int method, int inner_max, double inner_tol, int max_iters,
-                 double beta0, double gamma, double gamma_bar, double eta,
-                 double* out_fhat, double* out_beta, double* out_beta_bar, int* out_restart,
-                 double* out_ftrue, double* out_fblock, double* out_fhat0) {
+static int solve_impl(const data_term* D, int order, const int64_t* dims, double* const* A, int r,
+                      int her, int method, int inner_max, double inner_tol, int max_iters,
+                      double beta0, double gamma, double gamma_bar, double eta,
+                      double* out_fhat, double* out_beta, double* out_beta_bar, int* out_restart,
+                      double* out_ftrue, double* out_fblock, double* out_fhat0, double* out_factors) {
     if (check_shape(order, dims, r) || inner_max < 1 || max_iters < 0) return -1;
-    const int64_t total = numel_of(order, dims);
-    const double tnorm = oracle_norm_sq(T, total);
+    const double tnorm = D->U ? oracle_tucker_norm_sq(order, dims, D->cdims, D->T, D->U)
+                              : oracle_norm_sq(D->T, numel_of(order, dims));
     double* Ahat[MAXORD];
     double* G[MAXORD];
     double* M[MAXORD];
     double* Aprev = NULL;
     double* V = (double*)malloc(sizeof(double) * (size_t)r * (size_t)r);
-    int64_t maxrows = 0;
+    int64_t maxrows = 0, S = 0;
     for (int l = 0; l < order; ++l) {
         if (dims[l] > maxrows) maxrows = dims[l];
+        S += dims[l] * r;
         Ahat[l] = (double*)malloc(sizeof(double) * (size_t)dims[l] * (size_t)r);
         M[l] = (double*)malloc(sizeof(double) * (size_t)dims[l] * (size_t)r);
         G[l] = (double*)malloc(sizeof(double) * (size_t)r * (size_t)r);
@@ -432,7 +633,7 @@ int oracle_solve(int order, const int64_t* dims, const double* T, double* const*
     double state[3];
     state[0] = beta0;   /* beta_0 */
     state[1] = 1.0;     /* beta_bar_0 = 1 */
-    state[2] = oracle_objective_explicit(order, dims, T, (const double* const*)A, r);
+    state[2] = data_objective(D, order, dims, tnorm, (const double* const*)A, r);
     if (out_fhat0) *out_fhat0 = state[2];
 
     for (int k = 1; k <= max_iters; ++k) {
@@ -444,15 +645,24 @@ int oracle_solve(int order, const int64_t* dims, const double* T, double* const*
             for (int l = 0; l < order; ++l)
                 if (l != i) oracle_gram(Ahat[l], dims[l], r, G[l]);
             oracle_hadamard_grams((const double* const*)G, order, i, r, V);
-            oracle_mttkrp(order, dims, T, (const double* const*)Ahat, r, i, M[i]);
+            data_mttkrp(D, order, dims, (const double* const*)Ahat, r, i, M[i]);
             memcpy(Aprev, A[i], sizeof(double) * (size_t)n);          /* A_{k-1}^i */
             if (method == 0) oracle_hals(A[i], dims[i], r, M[i], V, inner_max, inner_tol);
-            else oracle_pgd(A[i], dims[i], r, M[i], V, inner_max, inner_tol);
+            else if (method == 1) oracle_pgd(A[i], dims[i], r, M[i], V, inner_max, inner_tol);
+            else oracle_nesterov(A[i], dims[i], r, M[i], V, inner_max, inner_tol);
             if (her) oracle_extrapolate(A[i], Aprev, beta, n, Ahat[i]);
             else memcpy(Ahat[i], A[i], sizeof(double) * (size_t)n);
             if (out_fblock)
                 out_fblock[(int64_t)(k - 1) * order + i] =
-                    oracle_objective_explicit(order, dims, T, (const double* const*)A, r);
+                    data_objective(D, order, dims, tnorm, (const double* const*)A, r);
+        }
+        if (out_factors) {
+            double* o = out_factors + (int64_t)(k - 1) * 3 * S;
+            for (int l = 0; l < order; ++l) {
+                memcpy(o, A[l], sizeof(double) * (size_t)dims[l] * (size_t)r);
+                memcpy(o + S, Ahat[l], sizeof(double) * (size_t)dims[l] * (size_t)r);
+                o += dims[l] * r;
+            }
         }
         /* F-hat_k = F(A_hat^1..A_hat^{N-1}, A^N): M and V of the last block
          * were formed against exactly those A_hat (Alg. 2, restart test). */
@@ -469,17 +679,52 @@ int oracle_solve(int order, const int64_t* dims, const double* T, double* const*
         } else {
             state[2] = fhat;
         }
+        if (out_factors) {
+            double* o = out_factors + (int64_t)(k - 1) * 3 * S + 2 * S;
+            for (int l = 0; l < order; ++l) {
+                memcpy(o, A[l], sizeof(double) * (size_t)dims[l] * (size_t)r);
+                o += dims[l] * r;
+            }
+        }
         if (out_fhat) out_fhat[k - 1] = fhat;
         if (out_beta) out_beta[k - 1] = state[0];
         if (out_beta_bar) out_beta_bar[k - 1] = state[1];
         if (out_restart) out_restart[k - 1] = restart;
         if (out_ftrue)
-            out_ftrue[k - 1] = oracle_objective_explicit(order, dims, T, (const double* const*)A, r);
+            out_ftrue[k - 1] = data_objective(D, order, dims, tnorm, (const double* const*)A, r);
     }
     for (int l = 0; l < order; ++l) { free(Ahat[l]); free(M[l]); free(G[l]); }
     free(Aprev);
     free(V);
     return 0;
+}
+
+/* Alg. 1 / Alg. 2 on a dense tensor T (see solve_impl for the outputs). */
+int oracle_solve(int order, const int64_t* dims, const double* T, double* const* A, int r,
+                 int her, int method, int inner_max, double inner_tol, int max_iters,
+                 double beta0, double gamma, double gamma_bar, double eta,
+                 double* out_fhat, double* out_beta, double* out_beta_bar, int* out_restart,
+                 double* out_ftrue, double* out_fblock, double* out_fhat0, double* out_factors) {
+    const data_term D = {T, NULL, NULL};
+    return solve_impl(&D, order, dims, A, r, her, method, inner_max, inner_tol, max_iters, beta0, gamma,
+                      gamma_bar, eta, out_fhat, out_beta, out_beta_bar, out_restart, out_ftrue, out_fblock,
+                      out_fhat0, out_factors);
+}
+
+/* Alg. 1 / Alg. 2 on the Tucker-format objective F_t of Appendix A (eq.
+ * objFunTucker): the data tensor is (U_0 (x) ... (x) U_{N-1}) G, entering only
+ * through oracle_tucker_mttkrp and oracle_tucker_norm_sq. */
+int oracle_solve_tucker(int order, const int64_t* dims, const int64_t* cdims, const double* G,
+                        const double* const* U, double* const* A, int r,
+                        int her, int method, int inner_max, double inner_tol, int max_iters,
+                        double beta0, double gamma, double gamma_bar, double eta,
+                        double* out_fhat, double* out_beta, double* out_beta_bar, int* out_restart,
+                        double* out_ftrue, double* out_fblock, double* out_fhat0, double* out_factors) {
+    if (!cdims || !U || check_shape(order, cdims, 1)) return -1;
+    const data_term D = {G, cdims, U};
+    return solve_impl(&D, order, dims, A, r, her, method, inner_max, inner_tol, max_iters, beta0, gamma,
+                      gamma_bar, eta, out_fhat, out_beta, out_beta_bar, out_restart, out_ftrue, out_fblock,
+                      out_fhat0, out_factors);
 }
 
 /* ------------------------------------------------------------------------ */

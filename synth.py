@@ -12,7 +12,7 @@ tensor built from them, Gaussian noise added and the result clipped at zero,
 ``T = max(0, T_clean + sigma * E)``.  Random initial factors are i.i.d. U[0,1]
 as in Sec. 4.1 ("Initialization, number of runs and plots").
 
-Readings that are not in the paper (documented in the design doc):
+Readings that are not in the paper:
   * the noise level is *relative*: ``sigma = noise_rel * ||T_clean||_F / sqrt(numel)``;
   * ``recipe="illcond"``: every column of a factor is one shared U[0,1] base
     column plus ``0.05 * U[0,1]`` (an ill-conditioned Gram, cf. Sec. 4.2's
@@ -118,3 +118,16 @@ WORKLOADS = {
     "hyper80_r16_sparse30": dict(dims=(80, 80, 80, 80), rank=16, noise_rel=1e-2, recipe="sparse30", seed=1237),
     "cube300_r32": dict(dims=(300, 300, 300), rank=32, noise_rel=1e-2, recipe="uniform", seed=1238),
 }
+
+
+def make_tucker(dims: Sequence[int], cdims: Sequence[int], seed: int,
+                dtype=np.float32) -> Tuple[np.ndarray, List[np.ndarray]]:
+    """Tucker-format data ``(G, U)`` (Appendix A): a core ``G`` of shape ``cdims``
+    and bases ``U_p`` of shape ``(dims[p], cdims[p])``, all i.i.d. U[0,1], so the
+    tensor they describe is nonnegative.  It stands in for the compressed form of
+    a data set too large to hold densely (the paper compresses a surveillance
+    video this way; that data set is not available here)."""
+    rng = _rng(seed)
+    G = rng.random(tuple(int(c) for c in cdims)).astype(dtype)
+    U = [rng.random((int(d), int(c))).astype(dtype) for d, c in zip(dims, cdims)]
+    return G, U
