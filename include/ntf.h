@@ -55,7 +55,7 @@ typedef enum {
 } ntf_status;
 
 typedef enum { NTF_F32 = 0, NTF_BF16 = 1 } ntf_dtype;
-typedef enum { NTF_HALS = 0, NTF_PGD = 1 } ntf_method;
+typedef enum { NTF_HALS = 0, NTF_PGD = 1, NTF_NESTEROV = 2 } ntf_method;
 
 #define NTF_MAX_ORDER 8
 #define NTF_MAX_RANK 64
@@ -68,6 +68,18 @@ typedef struct {
     int64_t ld;
     const void* data;
 } ntf_tensor;
+
+/* Tucker-format data (Appendix A, eq. objFunTucker): the tensor
+ * (U_0 (x) ... (x) U_{N-1}) G with dims[0] x ... x dims[N-1] entries, given by
+ * its core G -- an ntf_tensor of order N, NTF_F32, dims r_0 x ... x r_{N-1}
+ * with every Tucker rank r_p in [1, 64], laid out like any ntf_tensor -- and
+ * its bases U_p, device row-major dims[p] x r_p float32.  The expanded tensor
+ * is never formed: every use goes through the core and r_p x rank products. */
+typedef struct {
+    ntf_tensor core;
+    int64_t dims[NTF_MAX_ORDER];
+    const float* U[NTF_MAX_ORDER];
+} ntf_tucker;
 
 /* Device-resident HER state (Alg. 2 and Table 3).  Allocate sizeof(ntf_her_state)
  * bytes of device memory; initialise with ntf_her_state_init. */
@@ -85,7 +97,9 @@ typedef struct {
 /* Solver options.  ntf_opts_default() fills the paper's defaults:
  * HER on, HALS, inner_max = 1 (plain HALS sweep per block update),
  * inner_tol = 1e-2, beta0 = 0.5, gamma = 1.05, gamma_bar = 1.01, eta = 1.5
- * (Sec. 3.1 remarks; Sec. 4.1 "Parameter set up for HER"). */
+ * (Sec. 3.1 remarks; Sec. 4.1 "Parameter set up for HER"), no time or error
+ * target.  With HER on, the parameters must satisfy eq. HER:relation:
+ * 0 < beta0 < 1 < gamma_bar <= gamma <= eta. */
 typedef struct {
     int her;             /* 1: Alg. 2 (HER); 0: Alg. 1 (plain BCD) */
     ntf_method method;   /* block update */
@@ -96,6 +110,13 @@ typedef struct {
     ntf_dtype compute_dtype; /* NTF_BF16: cast T to bfloat16 once and stream that copy */
     int report_every;    /* > 0: explicit ||T - [[A_k]]||^2 every that many iterations */
     int use_graph;       /* 1: replay each outer iteration as a CUDA graph */
+    /* Stopping rules of ntf_solve* besides max_iters, tested every check_every
+     * iterations by reading one float64 (F-hat_k) back to the host.  The paper
+     * stops its runs at a wall-time budget (Sec. 4.1, "Initialization, number
+     * of runs and plots"); rel_tol stops at a target relative error instead. */
+    double max_seconds;  /* > 0: stop at the first check after this much wall time */
+    double rel_tol;      /* > 0: stop at the first check with sqrt(F-hat_k) / ||T||_F <= rel_tol */
+    int check_every;     /* iterations between checks; <= 0 means 10 */
 } ntf_opts;
 
 /* Host-side summary of a solve. */
@@ -237,6 +258,12 @@ NTF_API size_t ntf_bcd_workspace_bytes(int64_t rows, int rank);
  *   (a column with V(j,j) = 0 is left unchanged).
  * NTF_PGD (Sec. 2.2, eq. projgrad without in-block extrapolation):
  *   A <- max(0, A - (A V - M) / L),  L = lambda_max(V) (FP64 power iteration).
+ * NTF_NESTEROV (Sec. 2.1, AO-Nesterov: Nesterov's accelerated gradient on the
+ *   block NNLS; the paper names it without a formula, so it takes the
+ *   projected gradient step of eq. projgrad and the t_k momentum sequence
+ *   printed in Appendix B): with X_0 = Y_0 = A, t_0 = 1,
+ *   X_s = max(0, Y_{s-1} - (Y_{s-1} V - M) / L),  t_s = (1 + sqrt(1 + 4 t_{s-1}^2)) / 2,
+ *   Y_s = X_s + ((t_{s-1} - 1) / t_s) (X_s - X_{s-1});  A receives the last X_s.
  * Up to inner_max sweeps/steps; after sweep s >= 1 stop if
  * ||A_s - A_{s-1}||_F <= inner_tol ||A_1 - A_0||_F (Sec. 4.1).
  *   M: rows x rank float32; V: rank x rank float64;
@@ -292,7 +319,8 @@ NTF_API ntf_status ntf_residual_sq(const ntf_tensor* T, const float* const* fact
 /* ----------------------------------------------------------------------- */
 
 /* state_dev <- {beta0, beta_bar = 1, f_hat_prev = *f_hat0_dev, gamma, gamma_bar,
- * eta, counters 0}.  Requires 0 < beta0 <= 1 <= gamma_bar <= gamma <= eta. */
+ * eta, counters 0}.  Requires 0 < beta0 < 1 < gamma_bar <= gamma <= eta (Alg. 2;
+ * Sec. 3.1, eq. HER:relation). */
 NTF_API ntf_status ntf_her_state_init(ntf_her_state* state_dev, double beta0, double gamma, double gamma_bar, double eta,
                               const double* f_hat0_dev, void* stream);
 
@@ -304,6 +332,57 @@ NTF_API ntf_status ntf_her_state_init(ntf_her_state* state_dev, double beta0, do
  * pointers to rows[l] x rank float32 factors; rows: HOST array. */
 NTF_API ntf_status ntf_her_step(ntf_her_state* state_dev, float* const* A, float* const* A_hat, int order,
                         const int64_t* rows, int rank, const double* f_hat_dev, void* stream);
+
+/* ----------------------------------------------------------------------- */
+/* Tucker-format data (Appendix A)                                           */
+/* ----------------------------------------------------------------------- */
+
+/* Bytes of workspace ntf_tucker_mttkrp needs (0 if the arguments are invalid). */
+NTF_API size_t ntf_tucker_mttkrp_workspace_bytes(const ntf_tucker* X, int rank, int mode);
+
+/* out (dims[mode] x rank, float32) <- the MTTKRP of the Tucker-format tensor X,
+ * by the gradient formula of Appendix A:
+ *   out = U_mode * MTTKRP(G, {U_p^T A_p}_{p != mode}, mode),
+ * which equals the MTTKRP of the expanded tensor.  Cost: the projections
+ * U_p^T A_p (dims[p] x r_p x rank), one MTTKRP of the core, one expansion.
+ * Projections and expansion accumulate in FP32 over 64-row chunks combined in
+ * FP64 (fixed order).  factors: HOST array of `order` device pointers
+ * (factors[mode] unused).  workspace: 256-byte aligned device buffer of
+ * ws_bytes >= ntf_tucker_mttkrp_workspace_bytes().  Errors: NTF_EINVAL for an
+ * invalid core, Tucker rank > 64, rank, mode, pointer or workspace. */
+NTF_API ntf_status ntf_tucker_mttkrp(const ntf_tucker* X, const float* const* factors, int rank, int mode,
+                                     float* out, void* workspace, size_t ws_bytes, void* stream);
+
+/* Bytes of workspace ntf_tucker_norm_sq needs. */
+NTF_API size_t ntf_tucker_norm_workspace_bytes(const ntf_tucker* X);
+
+/* *out_dev (float64) <- ||(U_0 (x) ... (x) U_{N-1}) G||_F^2 without expanding:
+ * <G, G x_0 Q_0 ... x_{N-1} Q_{N-1}> with Q_p = U_p^T U_p, the mode products
+ * and the inner product in FP64. */
+NTF_API ntf_status ntf_tucker_norm_sq(const ntf_tucker* X, double* out_dev, void* workspace, size_t ws_bytes,
+                                      void* stream);
+
+/* ----------------------------------------------------------------------- */
+/* Tensor in host memory, streamed by slabs (Sec. 4, remark on data sets   */
+/* too large for the implementation's memory)                               */
+/* ----------------------------------------------------------------------- */
+
+/* Bytes of device workspace ntf_mttkrp_streamed needs for slabs of slab_rows
+ * mode-0 indices (slab_rows <= 0: the default, about 64 MB per slab): two
+ * staging buffers, the slab MTTKRP's workspace and one I_mode x rank partial. */
+NTF_API size_t ntf_mttkrp_streamed_workspace_bytes(const ntf_tensor* T_host, int rank, int mode, int64_t slab_rows);
+
+/* ntf_mttkrp of a tensor that stays in HOST memory (T_host->data; pinned memory
+ * gives full copy speed, pageable memory works but each copy is synchronous).
+ * The tensor is cut into slabs of slab_rows indices of mode 0; each slab is
+ * copied to the device with one cudaMemcpyAsync on a copy stream of the call,
+ * double-buffered against the MTTKRP of the previous slab on `stream`.  Mode 0
+ * writes its rows slab by slab; every other mode sums the slabs' partial
+ * MTTKRPs in slab order (bitwise reproducible, but summed in another order than
+ * ntf_mttkrp, so the two agree to FP32 rounding).  factors, out, workspace:
+ * device.  The call returns once everything is queued on `stream`. */
+NTF_API ntf_status ntf_mttkrp_streamed(const ntf_tensor* T_host, const float* const* factors, int rank, int mode,
+                                       float* out, void* workspace, size_t ws_bytes, int64_t slab_rows, void* stream);
 
 /* ----------------------------------------------------------------------- */
 /* Whole solver: Alg. 1 (her = 0) / Alg. 2 (her = 1)                          */
@@ -328,10 +407,35 @@ NTF_API ntf_status ntf_solve(const ntf_tensor* T, float* const* factors, int ran
 NTF_API ntf_status ntf_solve_host(const ntf_tensor* T_host, float* const* factors_host, int rank, const ntf_opts* opts,
                           ntf_report* report, void* stream);
 
+/* ntf_solve on the Tucker-format objective F_t of Appendix A (eq.
+ * objFunTucker): every MTTKRP goes through ntf_tucker_mttkrp, ||T||^2 through
+ * ntf_tucker_norm_sq, and F-hat_0 and the reported f_true_last are evaluated
+ * by the identity ||T||^2 - 2 <M_N, A_N> + sum(V_N (*) G(A_N)) with a fresh
+ * MTTKRP (the expanded tensor is never formed).  The general 9-launch
+ * iteration is used (no fused path); opts.compute_dtype must be NTF_F32. */
+NTF_API ntf_status ntf_solve_tucker(const ntf_tucker* X, float* const* factors, int rank, const ntf_opts* opts,
+                                    ntf_report* report, void* stream);
+
+/* ntf_solve with the tensor in HOST memory, streamed by slabs of mode 0 as in
+ * ntf_mttkrp_streamed for every MTTKRP, ||T||^2 and explicit residual.
+ * factors: HOST array of device pointers.  opts.compute_dtype must be NTF_F32
+ * (the host tensor's own dtype is streamed).  Allocates two staging buffers
+ * and the solver state on the device. */
+NTF_API ntf_status ntf_solve_streamed(const ntf_tensor* T_host, float* const* factors, int rank, const ntf_opts* opts,
+                                      ntf_report* report, int64_t slab_rows, void* stream);
+
 /* Stateful form of ntf_solve, for callers that step the solver themselves. */
 typedef struct ntf_solver ntf_solver;
 NTF_API ntf_status ntf_solver_create(ntf_solver** out, const ntf_tensor* T, float* const* factors, int rank,
                              const ntf_opts* opts, void* stream);
+/* Stateful solver on Tucker-format data (see ntf_solve_tucker) or on a tensor
+ * streamed from host memory (see ntf_solve_streamed); every other ntf_solver_*
+ * call works on them as on ntf_solver_create's solver (graphs are not used
+ * for the streamed form). */
+NTF_API ntf_status ntf_solver_create_tucker(ntf_solver** out, const ntf_tucker* X, float* const* factors, int rank,
+                                            const ntf_opts* opts, void* stream);
+NTF_API ntf_status ntf_solver_create_streamed(ntf_solver** out, const ntf_tensor* T_host, float* const* factors,
+                                              int rank, const ntf_opts* opts, int64_t slab_rows, void* stream);
 /* Run `iters` outer iterations on `stream` (asynchronous).  With opts.use_graph
  * and a non-default stream, a CUDA graph of 32 iterations is captured once and
  * replayed (the remainder runs eagerly); a run whose length matches a graph made

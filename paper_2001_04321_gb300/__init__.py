@@ -19,14 +19,16 @@ __all__ = [
     "NTFError", "lib", "load", "Opts", "Report", "mttkrp", "mttkrp_workspace_bytes", "gram",
     "hadamard_grams", "bcd_update", "her_extrapolate", "block_gradient", "CPLoss", "cp_loss", "objective", "residual_sq", "tensor_norm_sq",
     "to_bf16", "her_state_init", "her_step", "solve", "solve_host", "Solver", "launch_count",
-    "device_status", "HER_STATE_BYTES",
+    "device_status", "HER_STATE_BYTES", "Tucker", "tucker_mttkrp", "tucker_norm_sq", "solve_tucker",
+    "mttkrp_streamed", "solve_streamed",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libntf.so")
 
 NTF_F32, NTF_BF16 = 0, 1
-NTF_HALS, NTF_PGD = 0, 1
+NTF_HALS, NTF_PGD, NTF_NESTEROV = 0, 1, 2
+_METHODS = {"hals": NTF_HALS, "pgd": NTF_PGD, "nesterov": NTF_NESTEROV}
 _STATUS = {0: "NTF_OK", 1: "NTF_EINVAL", 2: "NTF_ENOMEM", 3: "NTF_ECUDA", 4: "NTF_ENUMERIC",
            5: "NTF_ETIMEOUT", 6: "NTF_ENOTSUP"}
 
@@ -45,13 +47,18 @@ class _Tensor(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("her", C.c_int), ("method", C.c_int), ("inner_max", C.c_int), ("inner_tol", C.c_double),
                 ("max_iters", C.c_int), ("beta0", C.c_double), ("gamma", C.c_double), ("gamma_bar", C.c_double),
-                ("eta", C.c_double), ("compute_dtype", C.c_int), ("report_every", C.c_int), ("use_graph", C.c_int)]
+                ("eta", C.c_double), ("compute_dtype", C.c_int), ("report_every", C.c_int), ("use_graph", C.c_int),
+                ("max_seconds", C.c_double), ("rel_tol", C.c_double), ("check_every", C.c_int)]
 
 
 class _Report(C.Structure):
     _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("f_hat_last", C.c_double),
                 ("f_true_last", C.c_double), ("rel_error", C.c_double), ("tnorm_sq", C.c_double),
                 ("beta_last", C.c_double), ("beta_bar_last", C.c_double), ("seconds", C.c_double)]
+
+
+class _Tucker(C.Structure):
+    _fields_ = [("core", _Tensor), ("dims", C.c_int64 * 8), ("U", C.c_void_p * 8)]
 
 
 class _HerState(C.Structure):
@@ -106,6 +113,21 @@ _SIGS = {
     "ntf_solver_mttkrp_time": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                          C.POINTER(C.c_double), _P]),
     "ntf_solver_destroy": (None, [_P]),
+    "ntf_tucker_mttkrp_workspace_bytes": (C.c_size_t, [C.POINTER(_Tucker), C.c_int, C.c_int]),
+    "ntf_tucker_mttkrp": (C.c_int, [C.POINTER(_Tucker), C.POINTER(_P), C.c_int, C.c_int, _P, _P, C.c_size_t, _P]),
+    "ntf_tucker_norm_workspace_bytes": (C.c_size_t, [C.POINTER(_Tucker)]),
+    "ntf_tucker_norm_sq": (C.c_int, [C.POINTER(_Tucker), _P, _P, C.c_size_t, _P]),
+    "ntf_mttkrp_streamed_workspace_bytes": (C.c_size_t, [C.POINTER(_Tensor), C.c_int, C.c_int, C.c_int64]),
+    "ntf_mttkrp_streamed": (C.c_int, [C.POINTER(_Tensor), C.POINTER(_P), C.c_int, C.c_int, _P, _P, C.c_size_t,
+                                      C.c_int64, _P]),
+    "ntf_solve_tucker": (C.c_int, [C.POINTER(_Tucker), C.POINTER(_P), C.c_int, C.POINTER(_Opts), C.POINTER(_Report),
+                                   _P]),
+    "ntf_solve_streamed": (C.c_int, [C.POINTER(_Tensor), C.POINTER(_P), C.c_int, C.POINTER(_Opts),
+                                     C.POINTER(_Report), C.c_int64, _P]),
+    "ntf_solver_create_tucker": (C.c_int, [C.POINTER(_P), C.POINTER(_Tucker), C.POINTER(_P), C.c_int,
+                                           C.POINTER(_Opts), _P]),
+    "ntf_solver_create_streamed": (C.c_int, [C.POINTER(_P), C.POINTER(_Tensor), C.POINTER(_P), C.c_int,
+                                             C.POINTER(_Opts), C.c_int64, _P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -258,7 +280,7 @@ def hadamard_grams(grams: Sequence, skip: int, out=None, stream=None):
 
 def bcd_update(A, M, V, method: str = "hals", inner_max: int = 1, inner_tol: float = 1e-2, workspace=None,
                stream=None):
-    """In-place block update of ``A`` (HALS or projected gradient)."""
+    """In-place block update of ``A``: "hals", "pgd" or "nesterov" (AO-Nesterov)."""
     torch = _torch()
     _require_cuda(A, "A", torch.float32)
     _require_cuda(M, "M", torch.float32)
@@ -267,7 +289,7 @@ def bcd_update(A, M, V, method: str = "hals", inner_max: int = 1, inner_tol: flo
     need = int(load().ntf_bcd_workspace_bytes(rows, r))
     if workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device=A.device)
-    m = NTF_HALS if method == "hals" else NTF_PGD
+    m = _METHODS[method]
     _check(load().ntf_bcd_update(m, _ptr(A), rows, r, _ptr(M), _ptr(V), inner_max, inner_tol, _ptr(workspace),
                                  workspace.numel(), _stream(stream)))
     return A
@@ -375,12 +397,15 @@ class Opts:
     compute_dtype: str = "f32"
     report_every: int = 0
     use_graph: bool = False
+    max_seconds: float = 0.0
+    rel_tol: float = 0.0
+    check_every: int = 0
 
     def c(self) -> _Opts:
         o = _Opts()
         load().ntf_opts_default(C.byref(o))
         o.her = int(self.her)
-        o.method = NTF_HALS if self.method == "hals" else NTF_PGD
+        o.method = _METHODS[self.method]
         o.inner_max = int(self.inner_max)
         o.inner_tol = float(self.inner_tol)
         o.max_iters = int(self.max_iters)
@@ -388,6 +413,9 @@ class Opts:
         o.compute_dtype = NTF_BF16 if self.compute_dtype == "bf16" else NTF_F32
         o.report_every = int(self.report_every)
         o.use_graph = int(self.use_graph)
+        o.max_seconds = float(self.max_seconds)
+        o.rel_tol = float(self.rel_tol)
+        o.check_every = int(self.check_every)
         return o
 
 
@@ -444,19 +472,44 @@ def solve_host(T_host, factors_host: List, opts: Optional[Opts] = None, stream=N
 
 
 class Solver:
-    """Stateful solver (``ntf_solver_*``): create once, ``run(k)`` asynchronously, ``report()``."""
+    """Stateful solver (``ntf_solver_*``): create once, ``run(k)`` asynchronously, ``report()``.
+    ``Solver.tucker(X, ...)`` and ``Solver.streamed(T_host, ...)`` build it on Tucker-format data or
+    on a tensor that stays in host memory."""
 
-    def __init__(self, T, factors: List, opts: Optional[Opts] = None, dims=None, ld: int = 0, stream=None):
+    def __init__(self, T, factors: List, opts: Optional[Opts] = None, dims=None, ld: int = 0, stream=None,
+                 _create=None):
         torch = _torch()
-        self._T = T
-        self._d = _tensor_desc(T, dims, ld)
         for A in factors:
             _require_cuda(A, "factor", torch.float32)
         self._o = (opts or Opts()).c()
         self._h = C.c_void_p()
-        _check(load().ntf_solver_create(C.byref(self._h), C.byref(self._d), _ptr_array(factors),
-                                        int(factors[0].shape[1]), C.byref(self._o), _stream(stream)))
+        if _create is None:
+            self._T = T
+            self._d = _tensor_desc(T, dims, ld)
+            _check(load().ntf_solver_create(C.byref(self._h), C.byref(self._d), _ptr_array(factors),
+                                            int(factors[0].shape[1]), C.byref(self._o), _stream(stream)))
+        else:
+            self._T = T
+            _create(self._h, self._o)
         self.rank = int(factors[0].shape[1])
+
+    @classmethod
+    def tucker(cls, X: "Tucker", factors: List, opts: Optional[Opts] = None, stream=None) -> "Solver":
+        def create(h, o):
+            _check(load().ntf_solver_create_tucker(C.byref(h), C.byref(X.c), _ptr_array(factors),
+                                                   int(factors[0].shape[1]), C.byref(o), _stream(stream)))
+        return cls(X, factors, opts, stream=stream, _create=create)
+
+    @classmethod
+    def streamed(cls, T_host, factors: List, opts: Optional[Opts] = None, slab_rows: int = 0,
+                 stream=None) -> "Solver":
+        d = _host_desc(T_host)
+
+        def create(h, o):
+            _check(load().ntf_solver_create_streamed(C.byref(h), C.byref(d), _ptr_array(factors),
+                                                     int(factors[0].shape[1]), C.byref(o), int(slab_rows),
+                                                     _stream(stream)))
+        return cls((T_host, d), factors, opts, stream=stream, _create=create)
 
     def run(self, iters: int, stream=None):
         _check(load().ntf_solver_run(self._h, int(iters), _stream(stream)))
@@ -493,6 +546,131 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------
+# Tucker-format data (Appendix A) and tensors streamed from host memory
+# ----------------------------------------------------------------------------
+class Tucker:
+    """Tucker-format data ``(U_0 (x) ... (x) U_{N-1}) G`` on the device: ``core`` is a float32 CUDA tensor
+    of shape (r_0, .., r_{N-1}), ``U`` the float32 CUDA bases (n_p, r_p).  The core is copied into a
+    buffer with 16-byte rows (the library's tensor layout)."""
+
+    def __init__(self, core, U: Sequence):
+        torch = _torch()
+        _require_cuda(core, "core", torch.float32)
+        cd = list(core.shape)
+        if len(U) != len(cd):
+            raise NTFError(1, "one basis per core mode")
+        ld = -(-cd[-1] // 4) * 4
+        rows = 1
+        for v in cd[:-1]:
+            rows *= int(v)
+        buf = torch.zeros((rows, ld), dtype=torch.float32, device=core.device)
+        buf[:, :cd[-1]] = core.reshape(rows, cd[-1])
+        self._core = buf
+        self.U = []
+        for p, u in enumerate(U):
+            _require_cuda(u, f"U_{p}", torch.float32)
+            if u.dim() != 2 or int(u.shape[1]) != cd[p]:
+                raise NTFError(1, f"U_{p} must be (n_{p}, {cd[p]})")
+            self.U.append(u)
+        self.dims = [int(u.shape[0]) for u in U]
+        self.core_dims = cd
+        c = _Tucker()
+        c.core = _tensor_desc(buf, cd, ld)
+        for p, u in enumerate(self.U):
+            c.dims[p] = self.dims[p]
+            c.U[p] = u.data_ptr()
+        self.c = c
+
+
+def tucker_mttkrp(X: Tucker, factors: Sequence, mode: int, out=None, stream=None):
+    """MTTKRP of the Tucker-format tensor through its core (Appendix A)."""
+    torch = _torch()
+    rank = int(factors[0 if mode != 0 else 1].shape[1])
+    dev = X.U[0].device
+    if out is None:
+        out = torch.empty((X.dims[mode], rank), dtype=torch.float32, device=dev)
+    need = int(load().ntf_tucker_mttkrp_workspace_bytes(C.byref(X.c), rank, mode))
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    ptrs = _ptr_array([None if l == mode else A for l, A in enumerate(factors)])
+    _check(load().ntf_tucker_mttkrp(C.byref(X.c), ptrs, rank, mode, _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def tucker_norm_sq(X: Tucker, out=None, stream=None):
+    torch = _torch()
+    dev = X.U[0].device
+    if out is None:
+        out = torch.empty((), dtype=torch.float64, device=dev)
+    ws = torch.empty(max(int(load().ntf_tucker_norm_workspace_bytes(C.byref(X.c))), 256), dtype=torch.uint8,
+                     device=dev)
+    _check(load().ntf_tucker_norm_sq(C.byref(X.c), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def solve_tucker(X: Tucker, factors: List, opts: Optional[Opts] = None, stream=None) -> Report:
+    """Alg. 2 (or Alg. 1) on the Tucker-format objective F_t, in place on the CUDA ``factors``."""
+    torch = _torch()
+    for A in factors:
+        _require_cuda(A, "factor", torch.float32)
+    o = (opts or Opts()).c()
+    rep = _Report()
+    _check(load().ntf_solve_tucker(C.byref(X.c), _ptr_array(factors), int(factors[0].shape[1]), C.byref(o),
+                                   C.byref(rep), _stream(stream)))
+    return _report(rep)
+
+
+def _host_desc(T_host) -> _Tensor:
+    """Describe a contiguous host float32/bfloat16 torch tensor whose last dim gives 16-byte rows."""
+    torch = _torch()
+    if not isinstance(T_host, torch.Tensor) or T_host.is_cuda or not T_host.is_contiguous():
+        raise NTFError(1, "T_host must be a contiguous host tensor")
+    d = _Tensor()
+    if T_host.dtype == torch.float32:
+        d.dtype = NTF_F32
+    elif T_host.dtype == torch.bfloat16:
+        d.dtype = NTF_BF16
+    else:
+        raise NTFError(1, "T_host must be float32 or bfloat16")
+    d.order = T_host.dim()
+    for i, v in enumerate(T_host.shape):
+        d.dims[i] = int(v)
+    d.ld = 0
+    d.data = T_host.data_ptr()
+    return d
+
+
+def mttkrp_streamed(T_host, factors: Sequence, mode: int, out=None, slab_rows: int = 0, stream=None):
+    """MTTKRP of a tensor in host memory, streamed to the device by slabs of mode 0."""
+    torch = _torch()
+    d = _host_desc(T_host)
+    rank = int(factors[0 if mode != 0 else 1].shape[1])
+    dev = factors[0 if mode != 0 else 1].device
+    if out is None:
+        out = torch.empty((int(T_host.shape[mode]), rank), dtype=torch.float32, device=dev)
+    need = int(load().ntf_mttkrp_streamed_workspace_bytes(C.byref(d), rank, mode, int(slab_rows)))
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    ptrs = _ptr_array([None if l == mode else A for l, A in enumerate(factors)])
+    # the staging buffers in ws are filled on the library's copy stream, but every copy completes
+    # before the work on `stream` that reads it, so ws may return to torch's stream-ordered cache
+    _check(load().ntf_mttkrp_streamed(C.byref(d), ptrs, rank, mode, _ptr(out), _ptr(ws), ws.numel(), int(slab_rows),
+                                      _stream(stream)))
+    return out
+
+
+def solve_streamed(T_host, factors: List, opts: Optional[Opts] = None, slab_rows: int = 0, stream=None) -> Report:
+    """Alg. 2 (or Alg. 1) with the tensor in host memory, in place on the CUDA ``factors``."""
+    torch = _torch()
+    d = _host_desc(T_host)
+    for A in factors:
+        _require_cuda(A, "factor", torch.float32)
+    o = (opts or Opts()).c()
+    rep = _Report()
+    _check(load().ntf_solve_streamed(C.byref(d), _ptr_array(factors), int(factors[0].shape[1]), C.byref(o),
+                                     C.byref(rep), int(slab_rows), _stream(stream)))
+    return _report(rep)
 
 
 from .autograd import CPLoss, cp_loss  # noqa: E402  (re-exported)

@@ -3,6 +3,7 @@
 #include "small.cuh"
 
 #include <atomic>
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -39,7 +40,7 @@ int* device_error_word() {
     return addr[dev];
 }
 
-static ntf_status check_device_ptr(const void* p, const char* what) {
+ntf_status check_device_ptr(const void* p, const char* what) {
     if (!p) return fail(NTF_EINVAL, std::string(what) + " is NULL");
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
@@ -110,6 +111,9 @@ void ntf_opts_default(ntf_opts* o) {
     o->compute_dtype = NTF_F32;
     o->report_every = 0;
     o->use_graph = 0;
+    o->max_seconds = 0.0;
+    o->rel_tol = 0.0;
+    o->check_every = 10;
 }
 
 int64_t ntf_bf16_ld(const ntf_tensor* T) {
@@ -199,14 +203,13 @@ ntf_status ntf_hadamard_grams(const double* const* grams, int order, int skip, i
 }
 
 size_t ntf_bcd_workspace_bytes(int64_t rows, int rank) {
-    (void)rank;
-    return rows < 1 ? 0 : bcd_workspace(rows);
+    return (rows < 1 || rank < 1 || rank > NTF_MAX_RANK) ? 0 : bcd_workspace(rows, rank);
 }
 
 ntf_status ntf_bcd_update(ntf_method method, float* A, int64_t rows, int rank, const float* M, const double* V,
                           int inner_max, double inner_tol, void* workspace, size_t ws_bytes, void* stream) {
     NTF_TRY(check_rank(rank));
-    if (method != NTF_HALS && method != NTF_PGD) return fail(NTF_EINVAL, "unknown method");
+    if (method != NTF_HALS && method != NTF_PGD && method != NTF_NESTEROV) return fail(NTF_EINVAL, "unknown method");
     if (rows < 1) return fail(NTF_EINVAL, "rows must be >= 1");
     if (inner_max < 1) return fail(NTF_EINVAL, "inner_max must be >= 1");
     if (!(inner_tol >= 0.0)) return fail(NTF_EINVAL, "inner_tol must be >= 0");
@@ -214,8 +217,8 @@ ntf_status ntf_bcd_update(ntf_method method, float* A, int64_t rows, int rank, c
     NTF_TRY(check_device_ptr(M, "M"));
     NTF_TRY(check_device_ptr(V, "V"));
     NTF_TRY(check_device_ptr(workspace, "workspace"));
-    if (ws_bytes < bcd_workspace(rows)) return fail(NTF_EINVAL, "workspace too small");
-    cudaError_t e = launch_bcd(method == NTF_HALS ? 0 : 1, A, rows, rank, M, V, inner_max, inner_tol, workspace,
+    if (ws_bytes < bcd_workspace(rows, rank)) return fail(NTF_EINVAL, "workspace too small");
+    cudaError_t e = launch_bcd((int)method, A, rows, rank, M, V, inner_max, inner_tol, workspace,
                                static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "ntf_bcd_update");
     return NTF_OK;
@@ -296,9 +299,9 @@ ntf_status ntf_residual_sq(const ntf_tensor* T, const float* const* factors, int
 
 ntf_status ntf_her_state_init(ntf_her_state* state_dev, double beta0, double gamma, double gamma_bar, double eta,
                               const double* f_hat0_dev, void* stream) {
-    if (!(beta0 > 0.0 && beta0 <= 1.0)) return fail(NTF_EINVAL, "beta0 must be in (0, 1]");
-    if (!(1.0 <= gamma_bar && gamma_bar <= gamma && gamma <= eta))
-        return fail(NTF_EINVAL, "need 1 <= gamma_bar <= gamma <= eta (Sec. 3.1, eq. HER:relation)");
+    if (!(beta0 > 0.0 && beta0 < 1.0)) return fail(NTF_EINVAL, "beta0 must be in (0, 1) (Alg. 2)");
+    if (!(1.0 < gamma_bar && gamma_bar <= gamma && gamma <= eta && std::isfinite(eta)))
+        return fail(NTF_EINVAL, "need 1 < gamma_bar <= gamma <= eta (Sec. 3.1, eq. HER:relation)");
     NTF_TRY(check_device_ptr(state_dev, "state_dev"));
     NTF_TRY(check_device_ptr(f_hat0_dev, "f_hat0_dev"));
     cudaError_t e = launch_her_init(state_dev, beta0, gamma, gamma_bar, eta, f_hat0_dev,

@@ -1,5 +1,5 @@
-// Step a3, the block updates: HALS column sweeps and projected-gradient steps, one thread per
-// row of A with the row in registers (R >= r wide).  Templates shared by bcd.cu (R <= 24),
+// Step a3, the block updates: HALS column sweeps, projected-gradient steps and AO-Nesterov
+// steps, one thread per row of A with the row in registers (R >= r wide).  Templates shared by bcd.cu (R <= 24),
 // bcd32.cu and bcd64.cu, which instantiate disjoint widths so that they compile in parallel.
 #pragma once
 
@@ -74,6 +74,37 @@ __device__ __forceinline__ float pgd_row(float (&a)[R], const float (&m)[R], con
     return d2;
 }
 
+// One AO-Nesterov step (Sec. 2.1, AO-Nesterov): the projected gradient step of eq. projgrad taken
+// at the extrapolated point y, then the momentum step with the weight w of the t_k sequence of
+// Appendix B:  x_new = max(0, y - (y V - m)/L),  y <- x_new + w (x_new - x),  x <- x_new.
+// Returns ||x_new - x||^2.
+template <int R>
+__device__ __forceinline__ float nesterov_row(float (&x)[R], float (&y)[R], const float (&m)[R], const float* Vs,
+                                              int r, float invL, float w) {
+    float nx[R];
+#pragma unroll (R > 32 ? 1 : R)
+    for (int j = 0; j < R; ++j) {
+        float g = -m[j];
+#pragma unroll
+        for (int l = 0; l < R; ++l) g = fmaf(y[l], Vs[l * R + j], g);
+        const float v = fmaxf(fmaf(-g, invL, y[j]), 0.f);
+        nx[j] = j < r ? v : 0.f;
+    }
+    float d2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const float d = nx[j] - x[j];
+        d2 = fmaf(d, d, d2);
+        y[j] = fmaf(w, d, nx[j]);
+        x[j] = nx[j];
+    }
+    return d2;
+}
+
+// t_s = (1 + sqrt(1 + 4 t_{s-1}^2)) / 2 with t_0 = 1 (Appendix B); the momentum weight after
+// step s is (t_{s-1} - 1) / t_s.
+__host__ __device__ __forceinline__ double nesterov_t_next(double t) { return 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t)); }
+
 template <int R>
 __device__ void stage_V(const double* __restrict__ V, int r, float* Vs) {
     for (int q = threadIdx.x; q < R * R; q += blockDim.x) {
@@ -82,7 +113,7 @@ __device__ void stage_V(const double* __restrict__ V, int r, float* Vs) {
     }
 }
 
-// Whole inner loop in one CTA (rows <= kBcdThreads).  method 0 = HALS, 1 = PGD.
+// Whole inner loop in one CTA (rows <= kBcdThreads).  method 0 = HALS, 1 = PGD, 2 = AO-Nesterov.
 template <int R>
 __global__ void __launch_bounds__(kBcdThreads) k_bcd_local(int method, float* __restrict__ A, int64_t rows, int r,
                                                            const float* __restrict__ M, const double* __restrict__ V,
@@ -102,13 +133,24 @@ __global__ void __launch_bounds__(kBcdThreads) k_bcd_local(int method, float* __
 #pragma unroll
         for (int p = 0; p < R; ++p) a[p] = m[p] = 0.f;
     }
-    const float invL = (method == 1 && Lptr && *Lptr > 0.0) ? (float)(1.0 / *Lptr) : 0.f;
+    const float invL = (method != 0 && Lptr && *Lptr > 0.0) ? (float)(1.0 / *Lptr) : 0.f;
+    float y[R];                       // AO-Nesterov: extrapolated point, Y_0 = X_0
+#pragma unroll
+    for (int p = 0; p < R; ++p) y[p] = a[p];
+    double t = 1.0;
     double delta1 = 0.0;
     int s = 0;
     for (;;) {
         ++s;
         float d2 = 0.f;
-        if (live) d2 = method == 0 ? hals_row<R>(a, m, Vs, r) : pgd_row<R>(a, m, Vs, r, invL);
+        if (method == 2) {
+            const double tn = nesterov_t_next(t);
+            const float w = (float)((t - 1.0) / tn);
+            t = tn;
+            if (live) d2 = nesterov_row<R>(a, y, m, Vs, r, invL, w);
+        } else if (live) {
+            d2 = method == 0 ? hals_row<R>(a, m, Vs, r) : pgd_row<R>(a, m, Vs, r, invL);
+        }
         const double tot = block_sum_d((double)d2, sbuf);
         if (s == 1) delta1 = tot;
         if (s >= inner_max || tot <= tol2 * delta1) break;
@@ -123,11 +165,14 @@ __global__ void __launch_bounds__(kBcdThreads) k_bcd_local(int method, float* __
 // One sweep/step across many CTAs.  Sweep s (1-based) first decides, from the
 // partial sums of sweeps 1 and s-1, whether the inner loop has stopped.
 // parts: [2][gridDim] doubles (by sweep parity) + [gridDim] for sweep 1; flag: stopped.
+// AO-Nesterov keeps its extrapolated point in Y (rows x r; read from A at s = 1) and takes
+// the momentum weight w of step s from the host.
 template <int R>
 __global__ void __launch_bounds__(kBcdThreads) k_bcd_sweep(int method, float* __restrict__ A, int64_t rows, int r,
                                                            const float* __restrict__ M, const double* __restrict__ V,
                                                            const double* __restrict__ Lptr, int s, double tol2,
-                                                           double* __restrict__ parts, int* __restrict__ stopped) {
+                                                           double* __restrict__ parts, int* __restrict__ stopped,
+                                                           float* __restrict__ Y, float w) {
     __shared__ float Vs[R * R];
     __shared__ double sbuf[33];
     __shared__ int stop_sh;
@@ -157,8 +202,17 @@ __global__ void __launch_bounds__(kBcdThreads) k_bcd_sweep(int method, float* __
         float a[R], m[R];
         load_row<R>(A, i, r, a);
         load_row<R>(M, i, r, m);
-        const float invL = (method == 1 && Lptr && *Lptr > 0.0) ? (float)(1.0 / *Lptr) : 0.f;
-        d2 = method == 0 ? hals_row<R>(a, m, Vs, r) : pgd_row<R>(a, m, Vs, r, invL);
+        const float invL = (method != 0 && Lptr && *Lptr > 0.0) ? (float)(1.0 / *Lptr) : 0.f;
+        if (method == 2) {
+            float y[R];
+            load_row<R>(s == 1 ? A : Y, i, r, y);
+            d2 = nesterov_row<R>(a, y, m, Vs, r, invL, w);
+#pragma unroll
+            for (int p = 0; p < R; ++p)
+                if (p < r) Y[i * r + p] = y[p];
+        } else {
+            d2 = method == 0 ? hals_row<R>(a, m, Vs, r) : pgd_row<R>(a, m, Vs, r, invL);
+        }
 #pragma unroll
         for (int p = 0; p < R; ++p)
             if (p < r) A[i * r + p] = a[p];
@@ -216,8 +270,9 @@ static __global__ void k_lambda_max(const double* __restrict__ V, int r, double*
 
 template <int R>
 static cudaError_t bcd_impl(int method, float* A, int64_t rows, int r, const float* M, const double* V,
-                            int inner_max, double tol, double* L, double* parts, int* stopped, cudaStream_t st) {
-    if (method == 1) {
+                            int inner_max, double tol, double* L, double* parts, int* stopped, float* Y,
+                            cudaStream_t st) {
+    if (method != 0) {
         k_lambda_max<<<1, 32, 0, st>>>(V, r, L);
         count_launch();
     }
@@ -228,16 +283,22 @@ static cudaError_t bcd_impl(int method, float* A, int64_t rows, int r, const flo
         return cudaGetLastError();
     }
     const int G = (int)((rows + kBcdThreads - 1) / kBcdThreads);
+    double t = 1.0;
     for (int s = 1; s <= inner_max; ++s) {
-        k_bcd_sweep<R><<<G, kBcdThreads, 0, st>>>(method, A, rows, r, M, V, L, s, tol2, parts, stopped);
+        const double tn = nesterov_t_next(t);
+        const float w = (float)((t - 1.0) / tn);
+        t = tn;
+        k_bcd_sweep<R><<<G, kBcdThreads, 0, st>>>(method, A, rows, r, M, V, L, s, tol2, parts, stopped, Y, w);
         count_launch();
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_bcd_r32(int method, float* A, int64_t rows, int r, const float* M, const double* V,
-                           int inner_max, double tol, double* L, double* parts, int* stopped, cudaStream_t st);
+                           int inner_max, double tol, double* L, double* parts, int* stopped, float* Y,
+                           cudaStream_t st);
 cudaError_t launch_bcd_r64(int method, float* A, int64_t rows, int r, const float* M, const double* V,
-                           int inner_max, double tol, double* L, double* parts, int* stopped, cudaStream_t st);
+                           int inner_max, double tol, double* L, double* parts, int* stopped, float* Y,
+                           cudaStream_t st);
 
 }  // namespace ntf

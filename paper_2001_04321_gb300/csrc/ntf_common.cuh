@@ -23,6 +23,8 @@ void set_error(const std::string& msg);
 ntf_status fail(ntf_status s, const std::string& msg);
 ntf_status cuda_fail(cudaError_t e, const char* where);
 void count_launch(int n = 1);
+// NTF_EINVAL unless p is a non-NULL device (or managed) pointer
+ntf_status check_device_ptr(const void* p, const char* what);
 
 #define NTF_CUDA_TRY(expr)                                         \
     do {                                                           \

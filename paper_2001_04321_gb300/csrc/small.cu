@@ -291,6 +291,24 @@ __global__ void k_sum_parts(const double* __restrict__ parts, int n, double* __r
 
 int stream_red_blocks() { return 4 * num_sms(); }
 
+cudaError_t launch_sum_parts(const double* parts, int n, double* out, cudaStream_t st) {
+    k_sum_parts<<<1, 256, 0, st>>>(parts, n, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// y += x elementwise (the slab partials of a streamed MTTKRP, summed in slab order)
+__global__ void k_add(float* __restrict__ y, const float* __restrict__ x, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] += x[i];
+}
+
+cudaError_t launch_add(float* y, const float* x, int64_t n, cudaStream_t st) {
+    k_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, x, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_norm_sq(const TensorView& v, double* parts, double* out, cudaStream_t st) {
     const int G = stream_red_blocks();
     if (v.dtype == NTF_F32)

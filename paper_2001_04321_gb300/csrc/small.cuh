@@ -25,7 +25,7 @@ size_t gram_smem(int r);
 cudaError_t launch_gram(const float* A, int64_t rows, int r, double* G, cudaStream_t st);
 cudaError_t launch_hadamard(const GramPtrs& P, int order, int skip, int r, double* V, cudaStream_t st);
 
-size_t bcd_workspace(int64_t rows);
+size_t bcd_workspace(int64_t rows, int r);
 cudaError_t launch_bcd(int method, float* A, int64_t rows, int r, const float* M, const double* V, int inner_max,
                        double tol, void* ws, cudaStream_t st);
 
@@ -40,6 +40,8 @@ cudaError_t launch_objective(const double* tn, const float* M, const float* A, i
                              double* out, double* G_out, cudaStream_t st);
 
 int stream_red_blocks();
+cudaError_t launch_sum_parts(const double* parts, int n, double* out, cudaStream_t st);   // fixed order
+cudaError_t launch_add(float* y, const float* x, int64_t n, cudaStream_t st);              // y += x
 cudaError_t launch_norm_sq(const TensorView& v, double* parts, double* out, cudaStream_t st);
 cudaError_t launch_residual_sq(const TensorView& v, int r, const float* W, int RP, const float* Ai, const float* Ac,
                                double* parts, double* out, cudaStream_t st);

@@ -4,6 +4,8 @@
 // taken on the device), so it can also be replayed as a CUDA graph.
 #include "small.cuh"
 #include "epilogue.cuh"
+#include "stream_host.cuh"
+#include "tucker.cuh"
 
 #include <cstdlib>
 
@@ -74,8 +76,21 @@ struct Solver {
     int g_iters = 0;
     int g_timing = 0;          // timing_every the graph was captured with
     int64_t g_kernels = 0;   // kernel nodes in the graph
+    // data term of the general path: a dense tensor in device memory, Tucker-format data
+    // (Appendix A), or a dense tensor in host memory streamed by slabs
+    enum class Src { Dense, Tucker, Streamed };
+    Src src = Src::Dense;
+    TuckerView tk;
+    TuckerPlan tkp[NTF_MAX_ORDER];
+    void* ws_tk = nullptr;
+    SlabStreamer* ss = nullptr;
+    // objective by the identity (Tucker data): Grams and V at A_k, the last mode's MTTKRP
+    double* Grep[NTF_MAX_ORDER] = {nullptr};
+    double* Vrep = nullptr;
+    float* Mrep = nullptr;
 
     ~Solver() {
+        delete ss;   // its streams and events; its workspace is one of allocs
         if (gexec) cudaGraphExecDestroy(gexec);
         for (auto& t : ev) {
             if (t.start) cudaEventDestroy(t.start);
@@ -342,10 +357,10 @@ struct Solver {
             if (e != cudaSuccess) return cuda_fail(e, "hadamard");
             const float* fac[NTF_MAX_ORDER];
             for (int l = 0; l < N; ++l) fac[l] = Ah[l];
-            ntf_status s = run_mttkrp(vs, plan[n], fac, M, ws_mt, st, &tm[n], next_timer());
+            ntf_status s = mttkrp_general(n, fac, M, st);
             if (s != NTF_OK) return s;
             if (use_her) NTF_CUDA_TRY(cudaMemcpyAsync(Aprev, A[n], sizeof(float) * rows * r, cudaMemcpyDeviceToDevice, st));
-            e = launch_bcd(o.method == NTF_HALS ? 0 : 1, A[n], rows, r, M, V, o.inner_max, o.inner_tol, ws_bcd, st);
+            e = launch_bcd((int)o.method, A[n], rows, r, M, V, o.inner_max, o.inner_tol, ws_bcd, st);
             if (e != cudaSuccess) return cuda_fail(e, "block update");
             if (use_her) {
                 e = launch_extrapolate(A[n], Aprev, &her->beta, rows * r, Ah[n], st);
@@ -378,7 +393,36 @@ struct Solver {
         return NTF_OK;
     }
 
+    // M_n against `fac` by the data term of this solver (the general path)
+    ntf_status mttkrp_general(int n, const float* const* fac, float* out, cudaStream_t st) {
+        if (src == Src::Tucker) return run_tucker_mttkrp(tk, tkp[n], fac, out, ws_tk, st, &tm[n]);
+        if (src == Src::Streamed) return ss->mttkrp(fac, n, out, st);
+        return run_mttkrp(vs, plan[n], fac, out, ws_mt, st, &tm[n], next_timer());
+    }
+
+    // ||T - [[A_k]]||^2 at the current factors: explicit for dense data (in device memory or
+    // streamed); for Tucker data by the identity of the restart test with a fresh MTTKRP
     ntf_status residual(const TensorView& v, double* out, cudaStream_t st) {
+        if (src != Src::Dense) {
+            float* facs[NTF_MAX_ORDER];
+            ntf_status s = current_factors(st, facs);
+            if (s != NTF_OK) return s;
+            const float* fac[NTF_MAX_ORDER];
+            for (int l = 0; l < N; ++l) fac[l] = facs[l];
+            if (src == Src::Streamed) return ss->residual_sq(fac, out, st);
+            GramPtrs gp{};
+            for (int l = 0; l < N; ++l) {
+                cudaError_t e = launch_gram(fac[l], vu.dims[l], r, Grep[l], st);
+                if (e != cudaSuccess) return cuda_fail(e, "gram");
+                gp.g[l] = Grep[l];
+            }
+            cudaError_t e = launch_hadamard(gp, N, N - 1, r, Vrep, st);
+            if (e != cudaSuccess) return cuda_fail(e, "hadamard");
+            s = run_tucker_mttkrp(tk, tkp[N - 1], fac, Mrep, ws_tk, st, &tm[N - 1]);
+            if (s != NTF_OK) return s;
+            e = launch_objective(&scal[0], Mrep, fac[N - 1], vu.dims[N - 1], r, Vrep, out, nullptr, st);
+            return e == cudaSuccess ? NTF_OK : cuda_fail(e, "objective");
+        }
         const int RP = (int)round_up(r, 4);
         float* W = static_cast<float*>(ws_res);
         const size_t woff = ((sizeof(float) * (size_t)v.n_o * RP) + 255) & ~size_t(255);
@@ -398,17 +442,101 @@ struct Solver {
 
 static ntf_status validate_opts(const ntf_opts& o) {
     if (o.her != 0 && o.her != 1) return fail(NTF_EINVAL, "opts.her must be 0 or 1");
-    if (o.method != NTF_HALS && o.method != NTF_PGD) return fail(NTF_EINVAL, "opts.method unknown");
+    if (o.method != NTF_HALS && o.method != NTF_PGD && o.method != NTF_NESTEROV)
+        return fail(NTF_EINVAL, "opts.method unknown");
     if (o.inner_max < 1) return fail(NTF_EINVAL, "opts.inner_max must be >= 1");
     if (!(o.inner_tol >= 0.0)) return fail(NTF_EINVAL, "opts.inner_tol must be >= 0");
     if (o.max_iters < 0) return fail(NTF_EINVAL, "opts.max_iters must be >= 0");
     if (o.compute_dtype != NTF_F32 && o.compute_dtype != NTF_BF16) return fail(NTF_EINVAL, "opts.compute_dtype unknown");
     if (o.her) {
-        if (!(o.beta0 > 0.0 && o.beta0 <= 1.0)) return fail(NTF_EINVAL, "opts.beta0 must be in (0, 1]");
-        if (!(1.0 <= o.gamma_bar && o.gamma_bar <= o.gamma && o.gamma <= o.eta))
-            return fail(NTF_EINVAL, "need 1 <= gamma_bar <= gamma <= eta (Sec. 3.1, eq. HER:relation)");
+        if (!(o.beta0 > 0.0 && o.beta0 < 1.0)) return fail(NTF_EINVAL, "opts.beta0 must be in (0, 1) (Alg. 2)");
+        if (!(1.0 < o.gamma_bar && o.gamma_bar <= o.gamma && o.gamma <= o.eta && std::isfinite(o.eta)))
+            return fail(NTF_EINVAL, "need 1 < gamma_bar <= gamma <= eta (Sec. 3.1, eq. HER:relation)");
     }
+    if (!(o.max_seconds >= 0.0) || !(o.rel_tol >= 0.0))
+        return fail(NTF_EINVAL, "opts.max_seconds and opts.rel_tol must be >= 0");
     return NTF_OK;
+}
+
+// Options, factor buffers and HER state shared by every data term.  dims: I_0..I_{N-1}.
+static ntf_status setup_common(Solver* S, int N, const int64_t* dims, float* const* factors, int rank,
+                               const ntf_opts* opts, cudaStream_t st) {
+    if (rank < 1 || rank > NTF_MAX_RANK) return fail(NTF_EINVAL, "rank must be in [1, 64]");
+    if (!factors) return fail(NTF_EINVAL, "factors is NULL");
+    cudaPointerAttributes pa;
+    for (int l = 0; l < N; ++l) {
+        if (!factors[l] || cudaPointerGetAttributes(&pa, factors[l]) != cudaSuccess ||
+            (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return fail(NTF_EINVAL, "factors must be device memory");
+        }
+    }
+    if (opts) S->o = *opts;
+    else ntf_opts_default(&S->o);
+    ntf_status s = validate_opts(S->o);
+    if (s != NTF_OK) return s;
+    {
+        const char* e = std::getenv("NTF_PDL");
+        S->pdl = !(e && e[0] == '0');
+    }
+    S->N = N;
+    S->r = rank;
+    const int r = rank;
+    int64_t maxrows = 0;
+    for (int l = 0; l < N; ++l) maxrows = std::max(maxrows, dims[l]);
+    for (int l = 0; l < N; ++l) {
+        const size_t fb = sizeof(float) * (size_t)dims[l] * r;
+        for (int k = 0; k < 2; ++k) {
+            if ((s = S->alloc((void**)&S->X[l][k], fb)) != NTF_OK) return s;
+            NTF_CUDA_TRY(cudaMemcpyAsync(S->X[l][k], factors[l], fb, cudaMemcpyDeviceToDevice, st));  // A_hat_0 = A_0
+            if ((s = S->alloc((void**)&S->GB[l][k], sizeof(double) * r * r)) != NTF_OK) return s;
+        }
+        S->A[l] = S->X[l][0];
+        S->G[l] = S->GB[l][0];
+        S->Ah[l] = S->o.her ? S->X[l][1] : S->X[l][0];
+        S->Gh[l] = S->o.her ? S->GB[l][1] : S->GB[l][0];
+    }
+    if ((s = S->alloc((void**)&S->cur, sizeof(int) * NTF_MAX_ORDER)) != NTF_OK) return s;
+    if ((s = S->alloc((void**)&S->iters_dev, 256)) != NTF_OK) return s;
+    NTF_CUDA_TRY(cudaMemsetAsync(S->cur, 0, sizeof(int) * NTF_MAX_ORDER, st));
+    NTF_CUDA_TRY(cudaMemsetAsync(S->iters_dev, 0, 256, st));
+    if ((s = S->alloc((void**)&S->Aprev, sizeof(float) * maxrows * r)) != NTF_OK) return s;
+    if ((s = S->alloc((void**)&S->M, sizeof(float) * maxrows * r)) != NTF_OK) return s;
+    if ((s = S->alloc((void**)&S->V, sizeof(double) * r * r)) != NTF_OK) return s;
+    if ((s = S->alloc((void**)&S->Vf, sizeof(float) * r * r)) != NTF_OK) return s;
+    if ((s = S->alloc((void**)&S->scal, sizeof(double) * 8)) != NTF_OK) return s;
+    if ((s = S->alloc((void**)&S->her, sizeof(ntf_her_state))) != NTF_OK) return s;
+    if ((s = S->alloc(&S->ws_bcd, bcd_workspace(maxrows, r))) != NTF_OK) return s;
+    if (!device_error_word()) return fail(NTF_ECUDA, "device error word unavailable");
+    cudaError_t e0 = launch_objective(nullptr, nullptr, nullptr, 1, r, nullptr, nullptr, nullptr, st);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "configure objective kernel");
+    return NTF_OK;
+}
+
+// Grams of A_0 (= A_hat_0), F-hat_0 = ||T - [[A_0]]||^2 and the HER state.  Needs scal[0] = ||T||^2.
+static ntf_status finish_setup(Solver* S, cudaStream_t st) {
+    const int N = S->N, r = S->r;
+    for (int l = 0; l < N; ++l) {
+        cudaError_t e = launch_gram(S->X[l][0], S->vu.dims[l], r, S->GB[l][0], st);
+        if (e != cudaSuccess) return cuda_fail(e, "gram");
+        NTF_CUDA_TRY(cudaMemcpyAsync(S->GB[l][1], S->GB[l][0], sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+    }
+    ntf_status s = S->residual(S->vs, &S->scal[3], st);
+    if (s != NTF_OK) return s;
+    cudaError_t e = launch_her_init(S->her, S->o.beta0, S->o.gamma, S->o.gamma_bar, S->o.eta, &S->scal[3], st);
+    if (e != cudaSuccess) return cuda_fail(e, "her init");
+    NTF_CUDA_TRY(cudaMemcpyAsync(&S->scal[1], &S->scal[3], sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return NTF_OK;
+}
+
+// Buffers of the objective by the identity (Tucker data): Grams, V and the last mode's MTTKRP at A_k.
+static ntf_status alloc_identity_buffers(Solver* S) {
+    const int N = S->N, r = S->r;
+    ntf_status s;
+    for (int l = 0; l < N; ++l)
+        if ((s = S->alloc((void**)&S->Grep[l], sizeof(double) * r * r)) != NTF_OK) return s;
+    if ((s = S->alloc((void**)&S->Vrep, sizeof(double) * r * r)) != NTF_OK) return s;
+    return S->alloc((void**)&S->Mrep, sizeof(float) * (size_t)S->vu.dims[N - 1] * r);
 }
 
 static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const* factors, int rank,
@@ -423,31 +551,13 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     };
     ntf_status s = make_view(T, &S->vu);
     if (s != NTF_OK) return bail(s);
-    if (rank < 1 || rank > NTF_MAX_RANK) return bail(fail(NTF_EINVAL, "rank must be in [1, 64]"));
-    if (!factors) return bail(fail(NTF_EINVAL, "factors is NULL"));
     cudaPointerAttributes pa;
     if (cudaPointerGetAttributes(&pa, S->vu.data) != cudaSuccess ||
         (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
         cudaGetLastError();
         return bail(fail(NTF_EINVAL, "tensor data must be device memory"));
     }
-    for (int l = 0; l < S->vu.order; ++l) {
-        if (!factors[l] || cudaPointerGetAttributes(&pa, factors[l]) != cudaSuccess ||
-            (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
-            cudaGetLastError();
-            return bail(fail(NTF_EINVAL, "factors must be device memory"));
-        }
-    }
-    if (opts) S->o = *opts;
-    else ntf_opts_default(&S->o);
-    s = validate_opts(S->o);
-    {
-        const char* e = std::getenv("NTF_PDL");
-        S->pdl = !(e && e[0] == '0');
-    }
-    if (s != NTF_OK) return bail(s);
-    S->N = S->vu.order;
-    S->r = rank;
+    if ((s = setup_common(S, S->vu.order, S->vu.dims, factors, rank, opts, st)) != NTF_OK) return bail(s);
     const int N = S->N, r = rank;
 
     // streamed tensor
@@ -467,28 +577,6 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
 
     int64_t maxrows = 0;
     for (int l = 0; l < N; ++l) maxrows = std::max(maxrows, S->vu.dims[l]);
-    for (int l = 0; l < N; ++l) {
-        const size_t fb = sizeof(float) * (size_t)S->vu.dims[l] * r;
-        for (int k = 0; k < 2; ++k) {
-            if ((s = S->alloc((void**)&S->X[l][k], fb)) != NTF_OK) return bail(s);
-            NTF_CUDA_TRY(cudaMemcpyAsync(S->X[l][k], factors[l], fb, cudaMemcpyDeviceToDevice, st));  // A_hat_0 = A_0
-            if ((s = S->alloc((void**)&S->GB[l][k], sizeof(double) * r * r)) != NTF_OK) return bail(s);
-        }
-        S->A[l] = S->X[l][0];
-        S->G[l] = S->GB[l][0];
-        S->Ah[l] = S->o.her ? S->X[l][1] : S->X[l][0];
-        S->Gh[l] = S->o.her ? S->GB[l][1] : S->GB[l][0];
-    }
-    if ((s = S->alloc((void**)&S->cur, sizeof(int) * NTF_MAX_ORDER)) != NTF_OK) return bail(s);
-    if ((s = S->alloc((void**)&S->iters_dev, 256)) != NTF_OK) return bail(s);
-    NTF_CUDA_TRY(cudaMemsetAsync(S->cur, 0, sizeof(int) * NTF_MAX_ORDER, st));
-    NTF_CUDA_TRY(cudaMemsetAsync(S->iters_dev, 0, 256, st));
-    if ((s = S->alloc((void**)&S->Aprev, sizeof(float) * maxrows * r)) != NTF_OK) return bail(s);
-    if ((s = S->alloc((void**)&S->M, sizeof(float) * maxrows * r)) != NTF_OK) return bail(s);
-    if ((s = S->alloc((void**)&S->V, sizeof(double) * r * r)) != NTF_OK) return bail(s);
-    if ((s = S->alloc((void**)&S->Vf, sizeof(float) * r * r)) != NTF_OK) return bail(s);
-    if ((s = S->alloc((void**)&S->scal, sizeof(double) * 8)) != NTF_OK) return bail(s);
-    if ((s = S->alloc((void**)&S->her, sizeof(ntf_her_state))) != NTF_OK) return bail(s);
     // one workspace region per mode: a mode's epilogue still reads its partials while the
     // next mode's operands are being written
     size_t ws = 0, off_mode[NTF_MAX_ORDER];
@@ -500,7 +588,6 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     }
     if ((s = S->alloc(&S->ws_mt, ws)) != NTF_OK) return bail(s);
     for (int n = 0; n < N; ++n) S->wsm[n] = static_cast<unsigned char*>(S->ws_mt) + off_mode[n];
-    if ((s = S->alloc(&S->ws_bcd, bcd_workspace(maxrows))) != NTF_OK) return bail(s);
     S->fused = S->o.method == NTF_HALS && S->o.inner_max == 1 && r <= 32;
     if (S->fused) {
         const int64_t blocks = epilogue_blocks(maxrows);
@@ -531,11 +618,6 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     S->ws_res_bytes = (((sizeof(float) * (size_t)S->vu.n_o * round_up(r, 4)) + 255) & ~size_t(255)) +
                       sizeof(double) * (size_t)std::max(stream_red_blocks(), 1);
     if ((s = S->alloc(&S->ws_res, S->ws_res_bytes)) != NTF_OK) return bail(s);
-    if (!device_error_word()) return bail(fail(NTF_ECUDA, "device error word unavailable"));
-    {
-        cudaError_t e0 = launch_objective(nullptr, nullptr, nullptr, 1, r, nullptr, nullptr, nullptr, st);
-        if (e0 != cudaSuccess) return bail(cuda_fail(e0, "configure objective kernel"));
-    }
 
     // ||T||^2 of the streamed and of the given tensor
     double* parts = reinterpret_cast<double*>(static_cast<unsigned char*>(S->ws_res) +
@@ -549,17 +631,81 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     } else {
         NTF_CUDA_TRY(cudaMemcpyAsync(&S->scal[4], &S->scal[0], sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
-    // Grams of A_0 (= A_hat_0)
-    for (int l = 0; l < N; ++l) {
-        e = launch_gram(S->X[l][0], S->vu.dims[l], r, S->GB[l][0], st);
-        if (e != cudaSuccess) return bail(cuda_fail(e, "gram"));
-        NTF_CUDA_TRY(cudaMemcpyAsync(S->GB[l][1], S->GB[l][0], sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+    if ((s = finish_setup(S, st)) != NTF_OK) return bail(s);
+    *out = S;
+    return NTF_OK;
+}
+
+// Tucker-format data (Appendix A): the general iteration with every MTTKRP through the core.
+static ntf_status create_solver_tucker(Solver** out, const ntf_tucker* X, float* const* factors, int rank,
+                                       const ntf_opts* opts, cudaStream_t st) {
+    *out = nullptr;
+    Solver* S = new Solver();
+    auto bail = [&](ntf_status s) {
+        delete S;
+        return s;
+    };
+    ntf_status s = make_tucker_view(X, &S->tk);
+    if (s != NTF_OK) return bail(s);
+    if ((s = check_device_ptr(S->tk.core.data, "Tucker core data")) != NTF_OK) return bail(s);
+    for (int p = 0; p < S->tk.order; ++p)
+        if ((s = check_device_ptr(S->tk.U[p], "Tucker basis U_p")) != NTF_OK) return bail(s);
+    // the expanded tensor's shape (never formed)
+    TensorView& v = S->vu;
+    v.order = S->tk.order;
+    for (int p = 0; p < v.order; ++p) v.dims[p] = S->tk.dims[p];
+    v.dtype = NTF_F32;
+    v.es = 4;
+    v.C = v.ld = v.dims[v.order - 1];
+    v.Ii = v.dims[v.order - 2];
+    v.n_o = 1;
+    for (int p = 0; p < v.order - 2; ++p) v.n_o *= v.dims[p];
+    v.data = nullptr;
+    S->vs = v;
+    S->src = Solver::Src::Tucker;
+    if ((s = setup_common(S, v.order, v.dims, factors, rank, opts, st)) != NTF_OK) return bail(s);
+    if (S->o.compute_dtype != NTF_F32) return bail(fail(NTF_EINVAL, "Tucker data needs opts.compute_dtype = NTF_F32"));
+    size_t ws = tucker_norm_workspace(S->tk);
+    for (int n = 0; n < S->N; ++n) {
+        if ((s = plan_tucker_mttkrp(S->tk, rank, n, &S->tkp[n])) != NTF_OK) return bail(s);
+        if ((s = configure_mttkrp(S->tk.core, S->tkp[n].core)) != NTF_OK) return bail(s);
+        ws = std::max(ws, S->tkp[n].total);
     }
-    // F-hat_0 = ||T - [[A_0]]||^2 explicitly (on the streamed tensor)
-    if ((s = S->residual(S->vs, &S->scal[3], st)) != NTF_OK) return bail(s);
-    e = launch_her_init(S->her, S->o.beta0, S->o.gamma, S->o.gamma_bar, S->o.eta, &S->scal[3], st);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "her init"));
-    NTF_CUDA_TRY(cudaMemcpyAsync(&S->scal[1], &S->scal[3], sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if ((s = S->alloc(&S->ws_tk, ws)) != NTF_OK) return bail(s);
+    if ((s = alloc_identity_buffers(S)) != NTF_OK) return bail(s);
+    if ((s = run_tucker_norm_sq(S->tk, &S->scal[0], S->ws_tk, st)) != NTF_OK) return bail(s);
+    NTF_CUDA_TRY(cudaMemcpyAsync(&S->scal[4], &S->scal[0], sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if ((s = finish_setup(S, st)) != NTF_OK) return bail(s);
+    *out = S;
+    return NTF_OK;
+}
+
+// Tensor in host memory, streamed by slabs of mode 0 for every pass over it.
+static ntf_status create_solver_streamed(Solver** out, const ntf_tensor* T_host, float* const* factors, int rank,
+                                         const ntf_opts* opts, int64_t slab_rows, cudaStream_t st) {
+    *out = nullptr;
+    Solver* S = new Solver();
+    auto bail = [&](ntf_status s) {
+        delete S;
+        return s;
+    };
+    ntf_status s = make_host_view(T_host, &S->vu);
+    if (s != NTF_OK) return bail(s);
+    S->vs = S->vu;
+    S->src = Solver::Src::Streamed;
+    if ((s = setup_common(S, S->vu.order, S->vu.dims, factors, rank, opts, st)) != NTF_OK) return bail(s);
+    if (S->o.compute_dtype != NTF_F32)
+        return bail(fail(NTF_EINVAL, "a streamed tensor is used in its own dtype: opts.compute_dtype = NTF_F32"));
+    S->o.use_graph = 0;
+    SlabLayout L;
+    if ((s = slab_layout(S->vu, rank, -1, slab_rows, &L)) != NTF_OK) return bail(s);
+    void* ws = nullptr;
+    if ((s = S->alloc(&ws, L.total)) != NTF_OK) return bail(s);
+    S->ss = new SlabStreamer();
+    if ((s = S->ss->init(S->vu, rank, -1, slab_rows, ws)) != NTF_OK) return bail(s);
+    if ((s = S->ss->norm_sq(&S->scal[0], st)) != NTF_OK) return bail(s);
+    NTF_CUDA_TRY(cudaMemcpyAsync(&S->scal[4], &S->scal[0], sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if ((s = finish_setup(S, st)) != NTF_OK) return bail(s);
     *out = S;
     return NTF_OK;
 }
@@ -648,6 +794,34 @@ static ntf_status run_solver(Solver* S, int iters, cudaStream_t st) {
     return NTF_OK;
 }
 
+// ntf_solve*: max_iters outer iterations, or fewer when a stopping rule of opts fires.  The rules
+// are tested every check_every iterations on one float64 read back to the host: the wall time
+// since t0 (the paper's runs stop at a time budget, Sec. 4.1) and sqrt(F-hat_k) / ||T||_F.
+static ntf_status run_until(Solver* S, cudaStream_t st, std::chrono::steady_clock::time_point t0) {
+    const ntf_opts& o = S->o;
+    if (!(o.max_seconds > 0.0) && !(o.rel_tol > 0.0)) return run_solver(S, o.max_iters, st);
+    const int m = o.check_every > 0 ? o.check_every : 10;
+    if (o.use_graph && st != nullptr && o.max_iters >= m && m <= kMaxGraphIters) {
+        ntf_status s = capture_graph(S, m, st);   // replayed by run_solver for every full chunk
+        if (s != NTF_OK) return s;
+    }
+    double h[2] = {0.0, 0.0};   // ||T_s||^2, F-hat_k
+    int done = 0;
+    while (done < o.max_iters) {
+        const int k = std::min(m, o.max_iters - done);
+        ntf_status s = run_solver(S, k, st);
+        if (s != NTF_OK) return s;
+        done += k;
+        NTF_CUDA_TRY(cudaMemcpyAsync(h, S->scal, sizeof(h), cudaMemcpyDeviceToHost, st));
+        NTF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (o.rel_tol > 0.0 && h[0] > 0.0 && std::sqrt(std::max(h[1], 0.0) / h[0]) <= o.rel_tol) break;
+        if (o.max_seconds > 0.0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() >= o.max_seconds)
+            break;
+    }
+    return NTF_OK;
+}
+
 static ntf_status solver_report(Solver* S, ntf_report* rep, cudaStream_t st) {
     ntf_status s = S->residual(S->vu, &S->scal[2], st);
     if (s != NTF_OK) return s;
@@ -670,6 +844,32 @@ static ntf_status solver_report(Solver* S, ntf_report* rep, cudaStream_t st) {
     if ((S->o.her && hs.numeric_error) || !std::isfinite(h[1]) || !std::isfinite(h[2]))
         return fail(NTF_ENUMERIC, "non-finite objective encountered");
     return NTF_OK;
+}
+
+// Runs a created solver to its stopping rule, copies A_k into `factors`, fills `report`
+// and deletes the solver.
+static ntf_status solve_and_release(Solver* S, float* const* factors, ntf_report* report, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    ntf_status s = NTF_OK;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_fail(e, "solver set-up");
+    auto t0 = std::chrono::steady_clock::now();
+    if (s == NTF_OK) s = run_until(S, st, t0);
+    if (s == NTF_OK) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "solve");
+    }
+    S->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    float* src[NTF_MAX_ORDER];
+    if (s == NTF_OK) s = S->current_factors(st, src);
+    for (int l = 0; l < S->N && s == NTF_OK; ++l) {
+        e = cudaMemcpyAsync(factors[l], src[l], sizeof(float) * S->vu.dims[l] * S->r, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) s = cuda_fail(e, "copy factors");
+    }
+    if (s == NTF_OK) s = solver_report(S, report, st);
+    delete S;
+    if (s == NTF_OK) s = ntf_device_status(stream);
+    return s;
 }
 
 }  // namespace ntf
@@ -764,27 +964,45 @@ ntf_status ntf_solve(const ntf_tensor* T, float* const* factors, int rank, const
     Solver* S = nullptr;
     ntf_status s = create_solver(&S, T, factors, rank, opts, st, nullptr);
     if (s != NTF_OK) return s;
-    NTF_CUDA_TRY(cudaStreamSynchronize(st));
-    auto t0 = std::chrono::steady_clock::now();
-    s = run_solver(S, S->o.max_iters, st);
-    if (s == NTF_OK) {
-        cudaError_t e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) s = cuda_fail(e, "solve");
-    }
-    S->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    float* src[NTF_MAX_ORDER];
-    if (s == NTF_OK) s = S->current_factors(st, src);
-    if (s == NTF_OK) {
-        for (int l = 0; l < S->N && s == NTF_OK; ++l) {
-            cudaError_t e = cudaMemcpyAsync(factors[l], src[l], sizeof(float) * S->vu.dims[l] * rank,
-                                            cudaMemcpyDeviceToDevice, st);
-            if (e != cudaSuccess) s = cuda_fail(e, "copy factors");
-        }
-    }
-    if (s == NTF_OK) s = solver_report(S, report, st);
-    delete S;
-    if (s == NTF_OK) s = ntf_device_status(stream);
-    return s;
+    return solve_and_release(S, factors, report, stream);
+}
+
+ntf_status ntf_solve_tucker(const ntf_tucker* X, float* const* factors, int rank, const ntf_opts* opts,
+                            ntf_report* report, void* stream) {
+    Solver* S = nullptr;
+    ntf_status s = create_solver_tucker(&S, X, factors, rank, opts, static_cast<cudaStream_t>(stream));
+    if (s != NTF_OK) return s;
+    return solve_and_release(S, factors, report, stream);
+}
+
+ntf_status ntf_solve_streamed(const ntf_tensor* T_host, float* const* factors, int rank, const ntf_opts* opts,
+                              ntf_report* report, int64_t slab_rows, void* stream) {
+    Solver* S = nullptr;
+    ntf_status s = create_solver_streamed(&S, T_host, factors, rank, opts, slab_rows, static_cast<cudaStream_t>(stream));
+    if (s != NTF_OK) return s;
+    return solve_and_release(S, factors, report, stream);
+}
+
+ntf_status ntf_solver_create_tucker(ntf_solver** out, const ntf_tucker* X, float* const* factors, int rank,
+                                    const ntf_opts* opts, void* stream) {
+    if (!out) return fail(NTF_EINVAL, "out is NULL");
+    *out = nullptr;
+    Solver* S = nullptr;
+    ntf_status s = create_solver_tucker(&S, X, factors, rank, opts, static_cast<cudaStream_t>(stream));
+    if (s != NTF_OK) return s;
+    *out = new ntf_solver{S};
+    return NTF_OK;
+}
+
+ntf_status ntf_solver_create_streamed(ntf_solver** out, const ntf_tensor* T_host, float* const* factors, int rank,
+                                      const ntf_opts* opts, int64_t slab_rows, void* stream) {
+    if (!out) return fail(NTF_EINVAL, "out is NULL");
+    *out = nullptr;
+    Solver* S = nullptr;
+    ntf_status s = create_solver_streamed(&S, T_host, factors, rank, opts, slab_rows, static_cast<cudaStream_t>(stream));
+    if (s != NTF_OK) return s;
+    *out = new ntf_solver{S};
+    return NTF_OK;
 }
 
 ntf_status ntf_solve_host(const ntf_tensor* T_host, float* const* factors_host, int rank, const ntf_opts* opts,
@@ -846,7 +1064,7 @@ ntf_status ntf_solve_host(const ntf_tensor* T_host, float* const* factors_host, 
         return s;
     }
     auto t0 = std::chrono::steady_clock::now();
-    s = run_solver(S, S->o.max_iters, st);
+    s = run_until(S, st, t0);
     float* src[NTF_MAX_ORDER];
     if (s == NTF_OK) s = S->current_factors(st, src);
     if (s == NTF_OK) {

@@ -120,14 +120,26 @@ WORKLOADS = {
 }
 
 
-def make_tucker(dims: Sequence[int], cdims: Sequence[int], seed: int,
+def make_tucker(dims: Sequence[int], cdims: Sequence[int], seed: int, rank: int = 0, noise: float = 0.0,
                 dtype=np.float32) -> Tuple[np.ndarray, List[np.ndarray]]:
     """Tucker-format data ``(G, U)`` (Appendix A): a core ``G`` of shape ``cdims``
-    and bases ``U_p`` of shape ``(dims[p], cdims[p])``, all i.i.d. U[0,1], so the
-    tensor they describe is nonnegative.  It stands in for the compressed form of
-    a data set too large to hold densely (the paper compresses a surveillance
-    video this way; that data set is not available here)."""
+    and bases ``U_p`` of shape ``(dims[p], cdims[p])`` with i.i.d. U[0,1] entries.
+    With ``rank = 0`` the core is i.i.d. U[0,1] too.  With ``rank > 0`` it is the
+    superdiagonal core of a rank-``rank`` CP tensor (ones at (q, .., q), q < rank)
+    plus ``noise`` times i.i.d. U[0,1], i.e. the Tucker form of a noisy nonnegative
+    rank-``rank`` CP tensor whose factors are the first columns of the bases.
+    Either way the tensor described is nonnegative.  It stands in for the
+    compressed form of a data set too large to hold densely (the paper compresses
+    a surveillance video this way; that data set is not available here)."""
     rng = _rng(seed)
-    G = rng.random(tuple(int(c) for c in cdims)).astype(dtype)
+    cdims = tuple(int(c) for c in cdims)
+    if rank > 0:
+        if rank > min(cdims):
+            raise ValueError("rank must not exceed the core dims")
+        G = noise * rng.random(cdims)
+        for q in range(rank):
+            G[(q,) * len(cdims)] += 1.0
+    else:
+        G = rng.random(cdims)
     U = [rng.random((int(d), int(c))).astype(dtype) for d, c in zip(dims, cdims)]
-    return G, U
+    return G.astype(dtype), U

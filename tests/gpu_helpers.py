@@ -32,3 +32,26 @@ def device_tensor(T, dtype="f32", pad_value=0.0):
     out = torch.empty(rows * ldb, dtype=torch.bfloat16, device="cuda")
     ntf._check(ntf.load().ntf_tensor_to_bf16(Cc.byref(d), ntf._ptr(out), ldb, ntf._stream(None)))
     return out, dims, ldb
+
+
+def check_trajectory(fh, rs, tr, tnorm_sq, min_k, atol_rel=1e-6, f_true=None, f_true_ref=None):
+    """Trajectory parity of a solver run against the oracle's trace ``tr`` from the same
+    initial factors.
+
+    F-hat agrees with the oracle's while every restart decision has matched, to an absolute
+    ``atol_rel ||T||^2``: F-hat is a difference of terms of size ||T||^2 formed from FP32
+    factors and MTTKRPs, so that is its resolution.  A first differing decision is allowed only
+    where the oracle's own margin F_k - F_{k-1} is below what the two sequences resolve
+    (2 atol): a tie that rounding decides.  The final objective always agrees within 1e-3
+    relative of the oracle's, plus the same resolution ``atol_rel ||T||^2``."""
+    atol = atol_rel * tnorm_sq
+    same = np.cumprod(np.asarray(rs) == tr.restart).astype(bool)
+    k = int(same.sum())
+    assert k >= min_k, f"decisions differ from iteration {k + 1}"
+    np.testing.assert_allclose(np.asarray(fh)[:k], tr.fhat[:k], rtol=0, atol=atol)
+    if k < len(rs):
+        prev = tr.fhat[k - 1] if k > 0 else tr.fhat0[0]
+        assert abs(tr.fhat[k] - prev) <= 2 * atol, "a restart decision differs away from a tie"
+    if f_true is not None:
+        assert abs(f_true - f_true_ref) <= 1e-3 * f_true_ref + atol, (f_true, f_true_ref, atol)
+    return k
