@@ -276,7 +276,9 @@ __global__ void __launch_bounds__(kEpiWarps * 32) k_epilogue(const EpiParams P) 
     const bool live = row < P.rows && lane < r;
     // Read before the wait for the stream: the current buffer index, the factor row,
     // V and beta.  They were written two or more launches back, and this launch starts
-    // only after the stream's own wait has seen those launches complete.  Loads go to
+    // only after the stream's own wait has seen those launches complete -- or, after an
+    // early stream (TcParams::early), while the epilogue two launches back may still run,
+    // which the host allows only where that epilogue writes none of them.  Loads go to
     // L2 (ld.global.cg), never to a possibly older L1 copy.
     const int cn = __ldcg(P.B.cur + n);
     float* A = P.B.X[n][cn];                      // in: A_{k-1}, out: A_k

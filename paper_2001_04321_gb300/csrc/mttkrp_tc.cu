@@ -212,6 +212,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
             }
         }
     }
+    // With P.early the producer and MMA warps do not wait for the kernel before this one and
+    // may trigger the launch of the kernel after it while that one still runs; the host sets
+    // early only where the kernel before writes nothing that this stream or the following
+    // epilogue reads before its own wait (Solver::early_stream_ok).
     if (!P.early || warp < 4) pdl_wait();
     pdl_trigger();
 

@@ -240,6 +240,17 @@ struct Solver {
         return NTF_OK;
     }
 
+    // Whether stream n may run ahead of the epilogue before it (TcParams::early).  Its producer
+    // and MMA warps then skip the programmatic-launch wait and trigger the launch of the
+    // epilogue after the stream while epilogue n-1 may still run.  That next epilogue reads
+    // cur[n], its factor row in X[n][cur], beta and V (when not formed by the stream) before
+    // its own wait, and the stream reads its packed operand and tile counter without waiting;
+    // so epilogue n-1 must write none of these.  The last mode's epilogue writes cur, beta,
+    // F-hat and the rows streams' packed operand (n = 0 excluded); epilogue N-2 writes the
+    // last-mode stream's packed operand (n = N-1 excluded); every other epilogue writes only
+    // its own factor buffers, Gram partials and objective partials.
+    static bool early_stream_ok(int n, int N) { return n >= 1 && n < N - 1; }
+
     TcParams direct_stream(int n) const {
         const bool use_her = o.her != 0;
         TcParams T{};
@@ -266,7 +277,7 @@ struct Solver {
         // mode 1's packed operand and buffer index come from the previous iteration's last
         // epilogue and its tile counter from that epilogue too: its tensor can stream in
         // while the mode-0 epilogue runs
-        T.early = n == 1 ? 1 : 0;
+        T.early = (n == 1 && early_stream_ok(n, N)) ? 1 : 0;
         GramJob& J = T.job;
         J.rr = r * r;
         J.order = N;
