@@ -22,7 +22,7 @@ from . import gram, hadamard_grams, mttkrp, objective, tensor_norm_sq, block_gra
 
 class CPLoss(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, T, dims: Optional[List[int]], ld: int, *factors):
+    def forward(ctx, T, dims: Optional[List[int]], ld: int, tnorm_sq, *factors):
         if dims is None:
             dims = list(T.shape)
         N = len(dims)
@@ -32,7 +32,9 @@ class CPLoss(torch.autograd.Function):
         grams = [gram(A) for A in F]
         M_last = mttkrp(T, F, N - 1, dims=dims, ld=ld)
         V_last = hadamard_grams(grams, N - 1)
-        tn = tensor_norm_sq(T, dims=dims, ld=ld)
+        # ||T||^2 is a property of the data: a caller that evaluates the loss repeatedly on one
+        # tensor passes it once (device float64 scalar) and saves a pass over T per forward
+        tn = tensor_norm_sq(T, dims=dims, ld=ld) if tnorm_sq is None else tnorm_sq
         f = objective(tn, M_last, F[N - 1], V_last)          # ||T - X||^2 (FP64, device)
         ctx.save_for_backward(T, M_last, *F)
         ctx.grams = grams
@@ -47,15 +49,16 @@ class CPLoss(torch.autograd.Function):
         g = grad_out.detach().to(torch.float64).reshape(())
         grads = []
         for n in range(N):
-            if not ctx.needs_input_grad[3 + n]:
+            if not ctx.needs_input_grad[4 + n]:
                 grads.append(None)
                 continue
             M = M_last if n == N - 1 else mttkrp(T, F, n, dims=ctx.dims, ld=ctx.ld)
             V = hadamard_grams(ctx.grams, n)
             grads.append(block_gradient(F[n], M, V, 1.0, scale_dev=g))
-        return (None, None, None, *grads)
+        return (None, None, None, None, *grads)
 
 
-def cp_loss(T, factors, dims=None, ld: int = 0):
-    """(1/2)||T - [[factors]]||^2 with a hand-written MTTKRP backward."""
-    return CPLoss.apply(T, dims, ld, *factors)
+def cp_loss(T, factors, dims=None, ld: int = 0, tnorm_sq=None):
+    """(1/2)||T - [[factors]]||^2 with a hand-written MTTKRP backward.  ``tnorm_sq``: optional
+    precomputed ||T||^2 (device float64 scalar, e.g. from ``tensor_norm_sq``)."""
+    return CPLoss.apply(T, dims, ld, tnorm_sq, *factors)

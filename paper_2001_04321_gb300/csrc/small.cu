@@ -73,6 +73,51 @@ cudaError_t launch_gram(const float* A, int64_t rows, int r, double* G, cudaStre
     return cudaGetLastError();
 }
 
+// Many-row Grams: each CTA accumulates kGramBlkRows rows as k_gram does (FP32 over 32-row
+// blocks, FP64 across them) into its own slot of upper-triangle partials; k_gram_sum adds the
+// slots in CTA order.  Deterministic, like the one-CTA kernel.
+constexpr int kGramBlkRows = 1024;
+
+__global__ void __launch_bounds__(kGramThreads) k_gram_part(const float* __restrict__ A, int64_t rows, int r,
+                                                            double* __restrict__ parts) {
+    extern __shared__ float sA[];
+    const int64_t r0 = (int64_t)blockIdx.x * kGramBlkRows;
+    const int64_t n = rows - r0 < kGramBlkRows ? rows - r0 : kGramBlkRows;
+    double acc[5] = {0, 0, 0, 0, 0};
+    gram_accumulate(A + r0 * r, n, r, sA, acc);
+    const int npairs = r * (r + 1) / 2;
+    int k = 0;
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x, ++k) parts[(int64_t)blockIdx.x * npairs + q] = acc[k];
+}
+
+__global__ void k_gram_sum(const double* __restrict__ parts, int nblk, int r, double* __restrict__ G) {
+    const int npairs = r * (r + 1) / 2;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= npairs) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += parts[(int64_t)b * npairs + q];
+    int p = 0, rem = q;
+    while (rem >= r - p) { rem -= r - p; ++p; }
+    const int c = p + rem;
+    G[p * r + c] = s;
+    G[c * r + p] = s;
+}
+
+size_t gram_parts_bytes(int64_t rows, int r) {
+    return sizeof(double) * (size_t)((rows + kGramBlkRows - 1) / kGramBlkRows) * (size_t)(r * (r + 1) / 2);
+}
+
+cudaError_t launch_gram_parts(const float* A, int64_t rows, int r, double* G, double* parts, cudaStream_t st) {
+    if (!parts || rows <= kGramBlkRows) return launch_gram(A, rows, r, G, st);
+    const int nblk = (int)((rows + kGramBlkRows - 1) / kGramBlkRows);
+    k_gram_part<<<nblk, kGramThreads, gram_smem(r), st>>>(A, rows, r, parts);
+    count_launch();
+    const int npairs = r * (r + 1) / 2;
+    k_gram_sum<<<(npairs + 255) / 256, 256, 0, st>>>(parts, nblk, r, G);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // V = Hadamard product of grams[l], l != skip
 __global__ void k_hadamard(GramPtrs P, int order, int skip, int r, double* __restrict__ V) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < r * r; q += gridDim.x * blockDim.x) {
@@ -293,6 +338,43 @@ int stream_red_blocks() { return 4 * num_sms(); }
 
 cudaError_t launch_sum_parts(const double* parts, int n, double* out, cudaStream_t st) {
     k_sum_parts<<<1, 256, 0, st>>>(parts, n, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Second layout of a 3-way tensor, last mode first: D[c][i0][i1] = S[i0][i1][c] (rows of D have
+// pitch ld_dst, the padding is left as it is).  32 x 32 tiles through shared memory, so both the
+// reads (along c) and the writes (along i1) are coalesced.
+template <typename E>
+__global__ void k_permute_last_first(const E* __restrict__ S, int64_t I0, int64_t I1, int64_t I2, int64_t ld,
+                                     E* __restrict__ D, int64_t ld_dst) {
+    __shared__ E tile[32][33];
+    const int64_t R = I0 * I1;
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;     // 32 x 8 threads
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t row = r0 + k, c = c0 + tx;
+        if (row < R && c < I2) tile[k][tx] = S[row * ld + c];
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t c = c0 + k, row = r0 + tx;
+        if (row < R && c < I2) {
+            const int64_t i0 = row / I1, i1 = row - i0 * I1;
+            D[(c * I0 + i0) * ld_dst + i1] = tile[tx][k];
+        }
+    }
+}
+
+cudaError_t launch_permute_last_first(const TensorView& v, void* dst, int64_t ld_dst, cudaStream_t st) {
+    const int64_t I0 = v.dims[0], I1 = v.dims[1], I2 = v.dims[2];
+    const dim3 grid((unsigned)((I2 + 31) / 32), (unsigned)((I0 * I1 + 31) / 32));
+    if (v.es == 4)
+        k_permute_last_first<uint32_t><<<grid, dim3(32, 8), 0, st>>>(static_cast<const uint32_t*>(v.data), I0, I1, I2,
+                                                                    v.ld, static_cast<uint32_t*>(dst), ld_dst);
+    else
+        k_permute_last_first<uint16_t><<<grid, dim3(32, 8), 0, st>>>(static_cast<const uint16_t*>(v.data), I0, I1, I2,
+                                                                    v.ld, static_cast<uint16_t*>(dst), ld_dst);
     count_launch();
     return cudaGetLastError();
 }

@@ -23,6 +23,9 @@ struct CopyPairs {
 
 size_t gram_smem(int r);
 cudaError_t launch_gram(const float* A, int64_t rows, int r, double* G, cudaStream_t st);
+// the same Gram over several CTAs for many rows (parts: gram_parts_bytes; NULL = one CTA)
+size_t gram_parts_bytes(int64_t rows, int r);
+cudaError_t launch_gram_parts(const float* A, int64_t rows, int r, double* G, double* parts, cudaStream_t st);
 cudaError_t launch_hadamard(const GramPtrs& P, int order, int skip, int r, double* V, cudaStream_t st);
 
 size_t bcd_workspace(int64_t rows, int r);
@@ -42,6 +45,8 @@ cudaError_t launch_objective(const double* tn, const float* M, const float* A, i
 int stream_red_blocks();
 cudaError_t launch_sum_parts(const double* parts, int n, double* out, cudaStream_t st);   // fixed order
 cudaError_t launch_add(float* y, const float* x, int64_t n, cudaStream_t st);              // y += x
+// 3-way tensor (I0, I1, I2) -> its copy with the last mode first, (I2, I0, I1), row pitch ld_dst
+cudaError_t launch_permute_last_first(const TensorView& v, void* dst, int64_t ld_dst, cudaStream_t st);
 cudaError_t launch_norm_sq(const TensorView& v, double* parts, double* out, cudaStream_t st);
 cudaError_t launch_residual_sq(const TensorView& v, int r, const float* W, int RP, const float* Ai, const float* Ac,
                                double* parts, double* out, cudaStream_t st);

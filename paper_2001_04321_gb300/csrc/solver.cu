@@ -69,6 +69,10 @@ struct Solver {
     bool prepped = false;
     __nv_bfloat16* packRows[2] = {nullptr, nullptr};   // packed A_{N-1} of buffer k (row streams)
     __nv_bfloat16* packLast = nullptr;                 // packed pairing A_{N-2} (last-mode stream)
+    // second layout of the streamed tensor with the last mode first, (I_2, I_0, I_1): the
+    // last mode's MTTKRP then runs the row-stream kernel (outer mode 0 of that layout)
+    bool perm = false;
+    TensorView vperm;
     // graph replay: one graph holds g_iters outer iterations (and, when timing is
     // on, the event records around each MTTKRP stream, read after the replay)
     cudaGraphExec_t gexec = nullptr;
@@ -88,6 +92,7 @@ struct Solver {
     double* Grep[NTF_MAX_ORDER] = {nullptr};
     double* Vrep = nullptr;
     float* Mrep = nullptr;
+    double* gparts = nullptr;   // partial sums of the many-row Grams of the general path
 
     ~Solver() {
         delete ss;   // its streams and events; its workspace is one of allocs
@@ -203,7 +208,7 @@ struct Solver {
         const MttkrpPlan& P = plan[n];
         EpiParams ep{};
         ep.B = fused_bufs();
-        ep.red = make_reduce_params(vs, P, reinterpret_cast<const float*>(ws + P.off_part),
+        ep.red = make_reduce_params(stream_view(n), P, reinterpret_cast<const float*>(ws + P.off_part),
                                     reinterpret_cast<const float*>(ws + P.off_W));
         ep.mode = n;
         ep.order = N;
@@ -240,6 +245,9 @@ struct Solver {
         return NTF_OK;
     }
 
+    // the tensor layout mode n's MTTKRP streams
+    const TensorView& stream_view(int n) const { return (perm && n == N - 1) ? vperm : vs; }
+
     // Whether stream n may run ahead of the epilogue before it (TcParams::early).  Its producer
     // and MMA warps then skip the programmatic-launch wait and trigger the launch of the
     // epilogue after the stream while epilogue n-1 may still run.  That next epilogue reads
@@ -260,6 +268,11 @@ struct Solver {
             T.FcTb[0] = reinterpret_cast<const unsigned char*>(packRows[0]);
             T.FcTb[1] = reinterpret_cast<const unsigned char*>(packRows[1]);
             T.fct_sel = N - 1;
+        } else if (perm) {
+            // last mode = outer mode 0 of the (I_2, I_0, I_1) layout: it contracts the I_1 index
+            // with the packed pairing A_1 and weights its I_0 rows by the pairing A_0
+            T.FcTb[0] = T.FcTb[1] = reinterpret_cast<const unsigned char*>(packLast);
+            T.fct_sel = 0;
         } else {
             T.FcTb[0] = T.FcTb[1] = reinterpret_cast<const unsigned char*>(packLast);
             T.fct_sel = 0;
@@ -274,6 +287,12 @@ struct Solver {
         T.Wb[1] = X[0][1];
         T.w_sel = 0;
         T.w_flip = (use_her && n > 0) ? 1 : 0;
+        if (perm && n == N - 1) {
+            T.Fib[0] = X[0][0];
+            T.Fib[1] = X[0][1];
+            T.fi_sel = 0;
+            T.fi_flip = use_her ? 1 : 0;
+        }
         // mode 1's packed operand and buffer index come from the previous iteration's last
         // epilogue and its tile counter from that epilogue too: its tensor can stream in
         // while the mode-0 epilogue runs
@@ -312,7 +331,7 @@ struct Solver {
             ntf_status s;
             if (direct) {
                 const TcParams T = direct_stream(n);
-                s = run_mttkrp_stream(vs, P, wsm[n], st, &tm[n], timer, pdl, &T);
+                s = run_mttkrp_stream(stream_view(n), P, wsm[n], st, &tm[n], timer, pdl, &T);
             } else {
                 s = run_mttkrp_stream(vs, P, wsm[n], st, &tm[n], timer, pdl);
             }
@@ -376,10 +395,10 @@ struct Solver {
             if (use_her) {
                 e = launch_extrapolate(A[n], Aprev, &her->beta, rows * r, Ah[n], st);
                 if (e != cudaSuccess) return cuda_fail(e, "extrapolate");
-                e = launch_gram(A[n], rows, r, G[n], st);
+                e = launch_gram_parts(A[n], rows, r, G[n], gparts, st);
                 if (e != cudaSuccess) return cuda_fail(e, "gram");
             }
-            e = launch_gram(Ah[n], rows, r, Gh[n], st);
+            e = launch_gram_parts(Ah[n], rows, r, Gh[n], gparts, st);
             if (e != cudaSuccess) return cuda_fail(e, "gram");
         }
         // F-hat_k = ||T||^2 - 2 <M_{N-1}, A_{N-1}> + sum(V_{N-1} (*) G(A_{N-1}))   (Alg. 2, restart test)
@@ -423,7 +442,7 @@ struct Solver {
             if (src == Src::Streamed) return ss->residual_sq(fac, out, st);
             GramPtrs gp{};
             for (int l = 0; l < N; ++l) {
-                cudaError_t e = launch_gram(fac[l], vu.dims[l], r, Grep[l], st);
+                cudaError_t e = launch_gram_parts(fac[l], vu.dims[l], r, Grep[l], gparts, st);
                 if (e != cudaSuccess) return cuda_fail(e, "gram");
                 gp.g[l] = Grep[l];
             }
@@ -518,6 +537,7 @@ static ntf_status setup_common(Solver* S, int N, const int64_t* dims, float* con
     if ((s = S->alloc((void**)&S->scal, sizeof(double) * 8)) != NTF_OK) return s;
     if ((s = S->alloc((void**)&S->her, sizeof(ntf_her_state))) != NTF_OK) return s;
     if ((s = S->alloc(&S->ws_bcd, bcd_workspace(maxrows, r))) != NTF_OK) return s;
+    if ((s = S->alloc((void**)&S->gparts, gram_parts_bytes(maxrows, r))) != NTF_OK) return s;
     if (!device_error_word()) return fail(NTF_ECUDA, "device error word unavailable");
     cudaError_t e0 = launch_objective(nullptr, nullptr, nullptr, 1, r, nullptr, nullptr, nullptr, st);
     if (e0 != cudaSuccess) return cuda_fail(e0, "configure objective kernel");
@@ -588,31 +608,79 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
 
     int64_t maxrows = 0;
     for (int l = 0; l < N; ++l) maxrows = std::max(maxrows, S->vu.dims[l]);
+    for (int n = 0; n < N; ++n) {
+        if ((s = plan_mttkrp(S->vs, r, n, &S->plan[n])) != NTF_OK) return bail(s);
+        if ((s = configure_mttkrp(S->vs, S->plan[n])) != NTF_OK) return bail(s);
+    }
+    S->fused = S->o.method == NTF_HALS && S->o.inner_max == 1 && r <= 32;
+    // every mode on the tensor cores, all BF16 or all 3xTF32 (the epilogues write one layout)
+    S->direct = S->fused && N == 3 && S->plan[0].tc && S->plan[1].tc && S->plan[2].tc &&
+                S->plan[0].tf32 == S->plan[2].tf32;
+    void* tperm = nullptr;
+    size_t tperm_bytes = 0;
+    {
+        // The last-mode kernel reads its tiles as 32- or 128-row column blocks and is the slowest
+        // of the three streams; a resident second copy of the tensor with the last mode first
+        // (I_2 x I_0 x I_1, one more numel x bytes of HBM) lets that MTTKRP run the row-stream
+        // kernel instead.  Off with NTF_PERM_LAST=0, or when the copy does not fit.
+        const char* env = std::getenv("NTF_PERM_LAST");
+        const bool want = !(env && env[0] == '0');
+        const TensorView& v = S->vs;
+        if (S->direct && want && ceil_div(v.dims[0] * v.dims[1], 32) <= 65535) {
+            TensorView vp = v;
+            vp.dims[0] = v.dims[2];
+            vp.dims[1] = v.dims[0];
+            vp.dims[2] = v.dims[1];
+            vp.C = v.dims[1];
+            vp.ld = round_up(vp.C, 16 / v.es);
+            vp.Ii = v.dims[0];
+            vp.n_o = v.dims[2];
+            MttkrpPlan pp;
+            tperm_bytes = (size_t)vp.rows() * vp.ld * vp.es;
+            if (plan_mttkrp(vp, r, 0, &pp) == NTF_OK && pp.tc && pp.tf32 == S->plan[0].tf32 &&
+                pp.kind == ModeKind::Outer && configure_mttkrp(vp, pp) == NTF_OK &&
+                cudaMalloc(&tperm, tperm_bytes) == cudaSuccess) {
+                S->allocs.push_back(tperm);
+                vp.data = tperm;
+                // pp.mode stays 0: the output is mode 0 of the (I_2, I_0, I_1) layout
+                S->vperm = vp;
+                S->plan[2] = pp;
+                S->perm = true;
+            } else {
+                cudaGetLastError();
+            }
+        }
+    }
     // one workspace region per mode: a mode's epilogue still reads its partials while the
     // next mode's operands are being written
     size_t ws = 0, off_mode[NTF_MAX_ORDER];
     for (int n = 0; n < N; ++n) {
-        if ((s = plan_mttkrp(S->vs, r, n, &S->plan[n])) != NTF_OK) return bail(s);
-        if ((s = configure_mttkrp(S->vs, S->plan[n])) != NTF_OK) return bail(s);
         off_mode[n] = ws;
         ws += (S->plan[n].total + 255) & ~size_t(255);
     }
     if ((s = S->alloc(&S->ws_mt, ws)) != NTF_OK) return bail(s);
     for (int n = 0; n < N; ++n) S->wsm[n] = static_cast<unsigned char*>(S->ws_mt) + off_mode[n];
-    S->fused = S->o.method == NTF_HALS && S->o.inner_max == 1 && r <= 32;
+    if (S->perm) {
+        NTF_CUDA_TRY(cudaMemsetAsync(tperm, 0, tperm_bytes, st));
+        cudaError_t e = launch_permute_last_first(S->vs, tperm, S->vperm.ld, st);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "last-mode-first copy"));
+        // the outer reduction of a 3-way tensor weights its single outer mode by 1
+        std::vector<float> ones((size_t)S->vperm.n_o * S->plan[2].RP, 1.0f);
+        NTF_CUDA_TRY(cudaMemcpy(S->wsm[2] + S->plan[2].off_W, ones.data(), sizeof(float) * ones.size(),
+                                cudaMemcpyHostToDevice));
+    }
     if (S->fused) {
         const int64_t blocks = epilogue_blocks(maxrows);
         if ((s = S->alloc((void**)&S->gpart, sizeof(float) * (size_t)blocks * 2 * r * r)) != NTF_OK) return bail(s);
         if ((s = S->alloc((void**)&S->ipart, sizeof(double) * (size_t)blocks)) != NTF_OK) return bail(s);
         if ((s = S->alloc((void**)&S->qpart, sizeof(double) * (size_t)blocks)) != NTF_OK) return bail(s);
-        // every mode on the tensor cores, all BF16 or all 3xTF32 (the epilogues write one layout)
-        S->direct = N == 3 && S->plan[0].tc && S->plan[1].tc && S->plan[2].tc &&
-                    S->plan[0].tf32 == S->plan[2].tf32;
         if (S->direct) {
             // packed operands, zero outside the factor rows and columns
             const size_t rows_b = (size_t)S->plan[0].n_kc * 2 * S->plan[0].RPH * 128;
-            const size_t last_b = (size_t)S->plan[2].nb *
-                                  (S->plan[2].tf32 ? (size_t)(2 * S->plan[2].RPH) * 128 : tc_last_b_bytes(S->plan[2].RPH));
+            const size_t last_b =
+                S->perm ? (size_t)S->plan[2].n_kc * 2 * S->plan[2].RPH * 128
+                        : (size_t)S->plan[2].nb *
+                              (S->plan[2].tf32 ? (size_t)(2 * S->plan[2].RPH) * 128 : tc_last_b_bytes(S->plan[2].RPH));
             for (int k = 0; k < 2; ++k) {
                 if ((s = S->alloc((void**)&S->packRows[k], rows_b)) != NTF_OK) return bail(s);
                 NTF_CUDA_TRY(cudaMemsetAsync(S->packRows[k], 0, rows_b, st));

@@ -159,3 +159,47 @@ def test_block_gradient_entry_point():
     with pytest.raises(ntf.NTFError):
         ntf.block_gradient(torch.zeros(4, 65, device="cuda"), torch.zeros(4, 65, device="cuda"),
                            torch.zeros(65, 65, dtype=torch.float64, device="cuda"))
+
+
+def test_cploss_with_precomputed_norm_and_cuda_graph():
+    # ||T||^2 passed in gives the same loss and gradients; the forward + backward can be
+    # captured as one CUDA graph and replayed, matching the eager result bit for bit
+    import torch
+    import paper_2001_04321_gb300 as ntf
+    dims, r = (40, 30, 20), 6
+    T, _ = synth.make_tensor(dims, r, 0.05, seed=21)
+    F = [A.astype(np.float32) for A in synth.make_init(dims, r, seed=21)]
+    Td, d, ld = device_tensor(T)
+    leaves = [_leaf(A) for A in F]
+    loss = ntf.cp_loss(Td, leaves, dims=d, ld=ld)
+    loss.backward()
+    ref = [A.grad.clone() for A in leaves]
+    tn = ntf.tensor_norm_sq(Td, dims=d, ld=ld)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    leaves2 = [_leaf(A) for A in F]
+
+    def step():
+        for A in leaves2:
+            A.grad = None
+        out = ntf.cp_loss(Td, leaves2, dims=d, ld=ld, tnorm_sq=tn)
+        out.backward()
+        return out
+
+    with torch.cuda.stream(st):
+        for _ in range(2):
+            l2 = step()
+    torch.cuda.synchronize()
+    assert l2.item() == loss.item()
+    assert all(torch.equal(a.grad, b) for a, b in zip(leaves2, ref))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st, capture_error_mode="thread_local"):
+        l3 = step()
+    for A in leaves2:
+        A.grad = None
+    g.replay()
+    torch.cuda.synchronize()
+    assert l3.item() == loss.item()
+    F64 = [A.astype(np.float64) for A in F]
+    for n in range(3):
+        assert rel_fro(ref[n].cpu().numpy(), oracle.cp_gradient(T.astype(np.float64), F64, n)) <= 1e-5

@@ -392,3 +392,25 @@ def test_her_parameters_outside_the_papers_ranges_are_rejected():
     for bad in (dict(beta0=1.0), dict(beta0=0.0), dict(gamma_bar=1.0, gamma=1.0), dict(gamma=2.0, eta=1.5)):
         with pytest.raises(ntf.NTFError):
             ntf.solve(buf, [A.clone() for A in Fd], ntf.Opts(max_iters=1, **bad), dims=d, ld=ld)
+
+
+@pytest.mark.parametrize("form", ["f32", "bf16"])
+def test_last_mode_first_layout_matches_last_mode_kernel(form, monkeypatch):
+    # the 3-way tensor-core path streams the last mode's MTTKRP from a second copy of the
+    # tensor with the last mode first (row-stream kernel); NTF_PERM_LAST=0 keeps the
+    # last-mode kernel.  Both agree with the oracle's factors, and with each other.
+    import paper_2001_04321_gb300 as ntf
+    dims, r, iters = (97, 130, 211), 12, 3
+    T, init, buf, d, ld, Fd = _setup(dims, r, 1e-2, 4800)
+    Tref = oracle.bf16_to_f64(oracle.round_bf16(T)) if form == "bf16" else T
+    _, tr = oracle.solve(Tref, init, iters, her=True, track_factors=True)
+    runs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("NTF_PERM_LAST", flag)
+        got, rs = _factors_after(buf, d, ld, Fd, iters, ntf.Opts(max_iters=iters, compute_dtype=form))
+        np.testing.assert_array_equal(rs, tr.restart)
+        for a, ref in zip(got[-1], tr.A_after(iters)):
+            assert rel_fro(a, ref) <= 1e-4
+        runs[flag] = got[-1]
+    for a, b in zip(runs["1"], runs["0"]):
+        assert rel_fro(a, b) <= 1e-4
