@@ -61,6 +61,19 @@ ntf_status run_mttkrp(const TensorView& v, const MttkrpPlan& plan, const float* 
                       void* workspace, cudaStream_t st, TmapCache* cache, StreamTimer* timer);
 
 int num_sms();
+
+// Packed tensor-core operand of the Khatri-Rao product of two factors (a merged pair of modes):
+// rows ka * Ib + kb, factors read from buffer cur[sel] ^ flip of each pair (cur NULL: a[0], b[0]).
+struct KrPack {
+    const float* a[2];
+    const float* b[2];
+    const int* cur;
+    int sel_a, flip_a, sel_b, flip_b;
+    int64_t Ia, Ib;
+    int r, RPH, n_kc, tf32;
+    void* out;
+};
+cudaError_t launch_pack_kr(const KrPack& K, cudaStream_t st);
 ReduceParams make_reduce_params(const TensorView& v, const MttkrpPlan& P, const float* part, const float* W);
 ntf_status configure_mttkrp(const TensorView& v, const MttkrpPlan& P);
 

@@ -282,6 +282,54 @@ __global__ void k_pack_fct_tf32(const float* __restrict__ A, int64_t rows, int r
     }
 }
 
+// The tensor-core operand of a merged pair of modes (a, b): the Khatri-Rao rows
+// K(ka Ib + kb, p) = A_a(ka, p) A_b(kb, p), packed exactly as k_pack_fct (bf16 hi | lo, 64-row
+// chunks) or k_pack_fct_tf32 (TF32 hi | lo, 32-row chunks) pack a factor.  The two factors are
+// read from the solver's buffers, chosen on the device: buffer cur[sel] ^ flip.
+__global__ void k_pack_kr(KrPack K) {
+    const float* Aa = K.cur ? K.a[__ldcg(K.cur + K.sel_a) ^ K.flip_a] : K.a[0];
+    const float* Ab = K.cur ? K.b[__ldcg(K.cur + K.sel_b) ^ K.flip_b] : K.b[0];
+    const int N = 2 * K.RPH;
+    const int kw = K.tf32 ? 32 : 64;                   // rows per chunk
+    const int64_t rows = K.Ia * K.Ib;
+    const int64_t total = (int64_t)K.n_kc * N * kw;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int kl = (int)(idx % kw);
+        const int n = (int)((idx / kw) % N);
+        const int64_t kc = idx / (kw * (int64_t)N);
+        const int64_t k = kc * kw + kl;
+        const int p = n < K.RPH ? n : n - K.RPH;
+        float x = 0.f;
+        if (k < rows && p < K.r) {
+            const int64_t ka = k / K.Ib, kb = k - ka * K.Ib;
+            x = Aa[ka * K.r + p] * Ab[kb * K.r + p];
+        }
+        if (K.tf32) {
+            uint32_t h;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+            const float hi = __uint_as_float(h);
+            uint32_t l;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+            const int64_t byte = (kc * N + n) * 128 + (((kl >> 2) ^ (n & 7)) << 4) + (kl & 3) * 4;
+            static_cast<float*>(K.out)[byte / 4] = n < K.RPH ? hi : __uint_as_float(l);
+        } else {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            const __nv_bfloat16 v = n < K.RPH ? hi : __float2bfloat16_rn(x - __bfloat162float(hi));
+            const int64_t byte = (kc * N + n) * 128 + (((kl >> 3) ^ (n & 7)) << 4) + (kl & 7) * 2;
+            static_cast<__nv_bfloat16*>(K.out)[byte / 2] = v;
+        }
+    }
+}
+
+cudaError_t launch_pack_kr(const KrPack& K, cudaStream_t st) {
+    const int64_t total = (int64_t)K.n_kc * 2 * K.RPH * (K.tf32 ? 32 : 64);
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 4096);
+    k_pack_kr<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(K);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // W(o,p) = prod_{l < N-2, l != skip} A_l(i_l(o), p)   (o in C order over modes 0..N-3)
 __global__ void k_weights(FactorPtrs F, Dims D, int order, int skip, int r, int RP, int64_t n_o,
                           float* __restrict__ W) {

@@ -342,39 +342,51 @@ cudaError_t launch_sum_parts(const double* parts, int n, double* out, cudaStream
     return cudaGetLastError();
 }
 
-// Second layout of a 3-way tensor, last mode first: D[c][i0][i1] = S[i0][i1][c] (rows of D have
-// pitch ld_dst, the padding is left as it is).  32 x 32 tiles through shared memory, so both the
-// reads (along c) and the writes (along i1) are coalesced.
+// A second layout of a tensor with its trailing modes [split, N) moved to the front:
+// D(i_split.., i_{N-1}, i_0.., i_{split-1}) = S(i_0, .., i_{N-1}), rows of D (the last index,
+// i_{split-1}) with pitch ld_dst, the padding left as it is.  S is read as an R x C' matrix (R over
+// the leading modes, C' over the trailing ones, whose last is pitched by ld) and written
+// transposed, through 32 x 32 tiles in shared memory so that both sides are coalesced.
 template <typename E>
-__global__ void k_permute_last_first(const E* __restrict__ S, int64_t I0, int64_t I1, int64_t I2, int64_t ld,
-                                     E* __restrict__ D, int64_t ld_dst) {
+__global__ void k_permute_split(const E* __restrict__ S, int64_t R, int64_t Cp, int64_t Cb, int64_t ld,
+                                int64_t I_in, E* __restrict__ D, int64_t ld_dst) {
     __shared__ E tile[32][33];
-    const int64_t R = I0 * I1;
     const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;     // 32 x 8 threads
+    const int64_t row_stride = (Cp / Cb) * ld;         // one leading index: all trailing entries
     for (int k = ty; k < 32; k += 8) {
         const int64_t row = r0 + k, c = c0 + tx;
-        if (row < R && c < I2) tile[k][tx] = S[row * ld + c];
+        if (row < R && c < Cp) tile[k][tx] = S[row * row_stride + (c / Cb) * ld + (c % Cb)];
     }
     __syncthreads();
+    const int64_t R_out = R / I_in;                    // leading modes other than the last one
     for (int k = ty; k < 32; k += 8) {
         const int64_t c = c0 + k, row = r0 + tx;
-        if (row < R && c < I2) {
-            const int64_t i0 = row / I1, i1 = row - i0 * I1;
-            D[(c * I0 + i0) * ld_dst + i1] = tile[tx][k];
+        if (row < R && c < Cp) {
+            const int64_t i0 = row / I_in, i1 = row - i0 * I_in;
+            D[(c * R_out + i0) * ld_dst + i1] = tile[tx][k];
         }
     }
 }
 
-cudaError_t launch_permute_last_first(const TensorView& v, void* dst, int64_t ld_dst, cudaStream_t st) {
-    const int64_t I0 = v.dims[0], I1 = v.dims[1], I2 = v.dims[2];
-    const dim3 grid((unsigned)((I2 + 31) / 32), (unsigned)((I0 * I1 + 31) / 32));
+bool permute_split_fits(const TensorView& v, int split) {
+    int64_t R = 1;
+    for (int l = 0; l < split; ++l) R *= v.dims[l];
+    return split >= 1 && split < v.order && (R + 31) / 32 <= 65535;
+}
+
+cudaError_t launch_permute_split(const TensorView& v, int split, void* dst, int64_t ld_dst, cudaStream_t st) {
+    int64_t R = 1, Cp = 1;
+    for (int l = 0; l < split; ++l) R *= v.dims[l];
+    for (int l = split; l < v.order; ++l) Cp *= v.dims[l];
+    const int64_t Cb = v.dims[v.order - 1], I_in = v.dims[split - 1];
+    const dim3 grid((unsigned)((Cp + 31) / 32), (unsigned)((R + 31) / 32));
     if (v.es == 4)
-        k_permute_last_first<uint32_t><<<grid, dim3(32, 8), 0, st>>>(static_cast<const uint32_t*>(v.data), I0, I1, I2,
-                                                                    v.ld, static_cast<uint32_t*>(dst), ld_dst);
+        k_permute_split<uint32_t><<<grid, dim3(32, 8), 0, st>>>(static_cast<const uint32_t*>(v.data), R, Cp, Cb, v.ld,
+                                                               I_in, static_cast<uint32_t*>(dst), ld_dst);
     else
-        k_permute_last_first<uint16_t><<<grid, dim3(32, 8), 0, st>>>(static_cast<const uint16_t*>(v.data), I0, I1, I2,
-                                                                    v.ld, static_cast<uint16_t*>(dst), ld_dst);
+        k_permute_split<uint16_t><<<grid, dim3(32, 8), 0, st>>>(static_cast<const uint16_t*>(v.data), R, Cp, Cb, v.ld,
+                                                               I_in, static_cast<uint16_t*>(dst), ld_dst);
     count_launch();
     return cudaGetLastError();
 }

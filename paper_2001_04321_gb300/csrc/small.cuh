@@ -45,8 +45,10 @@ cudaError_t launch_objective(const double* tn, const float* M, const float* A, i
 int stream_red_blocks();
 cudaError_t launch_sum_parts(const double* parts, int n, double* out, cudaStream_t st);   // fixed order
 cudaError_t launch_add(float* y, const float* x, int64_t n, cudaStream_t st);              // y += x
-// 3-way tensor (I0, I1, I2) -> its copy with the last mode first, (I2, I0, I1), row pitch ld_dst
-cudaError_t launch_permute_last_first(const TensorView& v, void* dst, int64_t ld_dst, cudaStream_t st);
+// copy of v with the trailing modes [split, N) first: (I_split..I_{N-1}, I_0..I_{split-1}), the
+// last mode of the copy (I_{split-1}) with row pitch ld_dst
+bool permute_split_fits(const TensorView& v, int split);
+cudaError_t launch_permute_split(const TensorView& v, int split, void* dst, int64_t ld_dst, cudaStream_t st);
 cudaError_t launch_norm_sq(const TensorView& v, double* parts, double* out, cudaStream_t st);
 cudaError_t launch_residual_sq(const TensorView& v, int r, const float* W, int RP, const float* Ai, const float* Ac,
                                double* parts, double* out, cudaStream_t st);

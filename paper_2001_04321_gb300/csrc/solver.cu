@@ -73,6 +73,13 @@ struct Solver {
     // last mode's MTTKRP then runs the row-stream kernel (outer mode 0 of that layout)
     bool perm = false;
     TensorView vperm;
+    // 4-way tensor-core path: modes 0 and 1 stream the tensor viewed as (I_0, I_1, I_2 I_3)
+    // against the packed Khatri-Rao rows of (A_2, A_3); modes 2 and 3 stream a resident copy laid
+    // out as (I_2, I_3, I_0 I_1) against those of (A_hat_0, A_hat_1).  Every MTTKRP still reads
+    // one full copy, but the contraction runs over I_2 I_3 (or I_0 I_1) columns instead of I_3.
+    bool direct4 = false;
+    TensorView vmode[NTF_MAX_ORDER];
+    void* packKR[2] = {nullptr, nullptr};   // [0]: rows of (A_2, A_3); [1]: rows of (A_hat_0, A_hat_1)
     // graph replay: one graph holds g_iters outer iterations (and, when timing is
     // on, the event records around each MTTKRP stream, read after the replay)
     cudaGraphExec_t gexec = nullptr;
@@ -246,7 +253,73 @@ struct Solver {
     }
 
     // the tensor layout mode n's MTTKRP streams
-    const TensorView& stream_view(int n) const { return (perm && n == N - 1) ? vperm : vs; }
+    const TensorView& stream_view(int n) const {
+        if (direct4) return vmode[n];
+        return (perm && n == N - 1) ? vperm : vs;
+    }
+
+    TcParams direct4_stream(int n) const {
+        const bool use_her = o.her != 0;
+        TcParams T = direct_stream(n);
+        const unsigned char* pk = reinterpret_cast<const unsigned char*>(packKR[n / 2]);
+        T.FcTb[0] = T.FcTb[1] = pk;
+        T.fct_sel = 0;
+        T.early = 0;
+        const int lead = n < 2 ? 0 : 2;     // the view's outer mode
+        // outer kind (n = 0, 2): its rows are mode lead + 1, not yet updated this iteration
+        T.Fib[0] = X[lead + 1][0];
+        T.Fib[1] = X[lead + 1][1];
+        T.fi_sel = lead + 1;
+        T.fi_flip = 0;
+        // inner kind (n = 1, 3): its outer index is mode lead, updated: the pairing A_hat
+        T.Wb[0] = X[lead][0];
+        T.Wb[1] = X[lead][1];
+        T.w_sel = lead;
+        T.w_flip = use_her ? 1 : 0;
+        return T;
+    }
+
+    // one outer iteration on the 4-way tensor-core path: two Khatri-Rao operand packs, and per
+    // mode a stream and an epilogue (the last epilogue takes F_hat, the decision and the flip)
+    ntf_status iterate_direct4(cudaStream_t st) {
+        const bool use_her = o.her != 0;
+        for (int n = 0; n < N; ++n) {
+            if (n == 0 || n == 2) {
+                // n = 0: (A_2, A_3) as the last decision left them; n = 2: the pairing A_hat of
+                // modes 0 and 1 (eq. NNLS_her_exact).  Launched in plain stream order.
+                KrPack K{};
+                const int a = n == 0 ? 2 : 0, b = a + 1;
+                K.a[0] = X[a][0];
+                K.a[1] = X[a][1];
+                K.b[0] = X[b][0];
+                K.b[1] = X[b][1];
+                K.cur = cur;
+                K.sel_a = a;
+                K.sel_b = b;
+                K.flip_a = K.flip_b = (n == 2 && use_her) ? 1 : 0;
+                K.Ia = vs.dims[a];
+                K.Ib = vs.dims[b];
+                K.r = r;
+                K.RPH = plan[n].RPH;
+                K.n_kc = plan[n].n_kc;
+                K.tf32 = plan[n].tf32 ? 1 : 0;
+                K.out = packKR[n / 2];
+                cudaError_t e = launch_pack_kr(K, st);
+                if (e != cudaSuccess) return cuda_fail(e, "Khatri-Rao operand");
+            }
+            StreamTimer* timer = next_timer();
+            const TcParams T = direct4_stream(n);
+            ntf_status s = run_mttkrp_stream(vmode[n], plan[n], wsm[n], st, &tm[n], timer, pdl, &T);
+            if (s != NTF_OK) return s;
+            EpiParams ep = make_epi(n);
+            const int nx = (n + 2) % N;
+            ep.sched_next = plan[nx].tile_slots ? reinterpret_cast<unsigned int*>(wsm[nx] + plan[nx].off_sched) : nullptr;
+            ep.v_from_stream = 1;
+            cudaError_t e = launch_epilogue(ep, st, pdl && !timer);
+            if (e != cudaSuccess) return cuda_fail(e, "epilogue");
+        }
+        return NTF_OK;
+    }
 
     // Whether stream n may run ahead of the epilogue before it (TcParams::early).  Its producer
     // and MMA warps then skip the programmatic-launch wait and trigger the launch of the
@@ -377,6 +450,7 @@ struct Solver {
     ntf_status iterate(cudaStream_t st) {
         timed_now = timing_every > 0 && (iter_seq % timing_every) == 0;
         ++iter_seq;
+        if (direct4) return iterate_direct4(st);
         if (fused) return iterate_fused(st);
         const bool use_her = o.her != 0;
         for (int n = 0; n < N; ++n) {
@@ -626,7 +700,7 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
         const char* env = std::getenv("NTF_PERM_LAST");
         const bool want = !(env && env[0] == '0');
         const TensorView& v = S->vs;
-        if (S->direct && want && ceil_div(v.dims[0] * v.dims[1], 32) <= 65535) {
+        if (S->direct && want && permute_split_fits(v, 2)) {
             TensorView vp = v;
             vp.dims[0] = v.dims[2];
             vp.dims[1] = v.dims[0];
@@ -651,6 +725,51 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
             }
         }
     }
+    void* t4 = nullptr;
+    {
+        // 4-way: merged-pair views (see Solver::direct4).  Needs unpadded rows for the merges,
+        // every mode on the tensor cores in one form, and room for the second layout; off with
+        // NTF_DIRECT4=0.
+        const char* env = std::getenv("NTF_DIRECT4");
+        const TensorView& v = S->vs;
+        if (S->fused && N == 4 && !(env && env[0] == '0') && v.ld == v.dims[3] && (v.dims[1] * v.es) % 16 == 0 &&
+            permute_split_fits(v, 2)) {
+            auto view3 = [&](int64_t a, int64_t b, int64_t c, const void* data) {
+                TensorView w = v;
+                w.order = 3;
+                w.dims[0] = a;
+                w.dims[1] = b;
+                w.dims[2] = c;
+                for (int l = 3; l < NTF_MAX_ORDER; ++l) w.dims[l] = 0;
+                w.C = w.ld = c;
+                w.Ii = b;
+                w.n_o = a;
+                w.data = data;
+                return w;
+            };
+            const int64_t I0 = v.dims[0], I1 = v.dims[1], I2 = v.dims[2], I3 = v.dims[3];
+            TensorView w1 = view3(I0, I1, I2 * I3, v.data), w2 = view3(I2, I3, I0 * I1, nullptr);
+            MttkrpPlan q[4];
+            bool ok = plan_mttkrp(w1, r, 0, &q[0]) == NTF_OK && plan_mttkrp(w1, r, 1, &q[1]) == NTF_OK &&
+                      plan_mttkrp(w2, r, 0, &q[2]) == NTF_OK && plan_mttkrp(w2, r, 1, &q[3]) == NTF_OK;
+            for (int k = 0; k < 4 && ok; ++k)
+                ok = q[k].tc && q[k].tf32 == q[0].tf32 && q[k].kind == (k % 2 ? ModeKind::Inner : ModeKind::Outer);
+            const size_t bytes = (size_t)v.numel() * v.es;
+            if (ok && configure_mttkrp(w1, q[0]) == NTF_OK && configure_mttkrp(w1, q[1]) == NTF_OK &&
+                configure_mttkrp(w2, q[2]) == NTF_OK && configure_mttkrp(w2, q[3]) == NTF_OK &&
+                cudaMalloc(&t4, bytes) == cudaSuccess) {
+                S->allocs.push_back(t4);
+                w2.data = t4;
+                for (int k = 0; k < 4; ++k) S->plan[k] = q[k];
+                S->vmode[0] = S->vmode[1] = w1;
+                S->vmode[2] = S->vmode[3] = w2;
+                S->direct4 = true;
+                S->prepped = true;     // no preparation kernel on this path
+            } else {
+                cudaGetLastError();
+            }
+        }
+    }
     // one workspace region per mode: a mode's epilogue still reads its partials while the
     // next mode's operands are being written
     size_t ws = 0, off_mode[NTF_MAX_ORDER];
@@ -662,12 +781,27 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     for (int n = 0; n < N; ++n) S->wsm[n] = static_cast<unsigned char*>(S->ws_mt) + off_mode[n];
     if (S->perm) {
         NTF_CUDA_TRY(cudaMemsetAsync(tperm, 0, tperm_bytes, st));
-        cudaError_t e = launch_permute_last_first(S->vs, tperm, S->vperm.ld, st);
+        cudaError_t e = launch_permute_split(S->vs, 2, tperm, S->vperm.ld, st);
         if (e != cudaSuccess) return bail(cuda_fail(e, "last-mode-first copy"));
         // the outer reduction of a 3-way tensor weights its single outer mode by 1
         std::vector<float> ones((size_t)S->vperm.n_o * S->plan[2].RP, 1.0f);
         NTF_CUDA_TRY(cudaMemcpy(S->wsm[2] + S->plan[2].off_W, ones.data(), sizeof(float) * ones.size(),
                                 cudaMemcpyHostToDevice));
+    }
+    if (S->direct4) {
+        // the (I_2, I_3, I_0, I_1) copy, the packed Khatri-Rao operands (zero padded) and the
+        // outer reductions' unit weights
+        cudaError_t e = launch_permute_split(S->vs, 2, t4, S->vs.dims[1], st);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "second layout"));
+        for (int k = 0; k < 2; ++k) {
+            const MttkrpPlan& P = S->plan[2 * k];
+            const size_t b = (size_t)P.n_kc * 2 * P.RPH * 128;
+            if ((s = S->alloc(&S->packKR[k], b)) != NTF_OK) return bail(s);
+            NTF_CUDA_TRY(cudaMemsetAsync(S->packKR[k], 0, b, st));
+            std::vector<float> ones((size_t)S->vmode[2 * k].n_o * P.RP, 1.0f);
+            NTF_CUDA_TRY(cudaMemcpy(S->wsm[2 * k] + P.off_W, ones.data(), sizeof(float) * ones.size(),
+                                    cudaMemcpyHostToDevice));
+        }
     }
     if (S->fused) {
         const int64_t blocks = epilogue_blocks(maxrows);
@@ -687,6 +821,8 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
             }
             if ((s = S->alloc((void**)&S->packLast, last_b)) != NTF_OK) return bail(s);
             NTF_CUDA_TRY(cudaMemsetAsync(S->packLast, 0, last_b, st));
+        }
+        if (S->direct || S->direct4) {
             // every epilogue resets the counter of the stream two launches ahead; the first
             // iteration's streams start from these
             for (int n = 0; n < N; ++n)

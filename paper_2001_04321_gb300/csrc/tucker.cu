@@ -41,15 +41,20 @@ __global__ void __launch_bounds__(kProjThreads) k_project(const float* __restric
     }
 }
 
-// out[o] = sum over chunks c, in order, of part[c][o], in FP64
+// out[o] = sum over chunks c of part[c][o] in FP64: one warp per output, lane l takes chunks
+// l, l + 32, ... in order, then a fixed butterfly (independent loads, same order every run)
 __global__ void k_project_sum(const float* __restrict__ part, int nchunks, int n_out, float* __restrict__ outf,
                               double* __restrict__ outd) {
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= n_out) return;
+    const int o = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (o >= n_out) return;   // whole warps leave together
     double s = 0.0;
-    for (int c = 0; c < nchunks; ++c) s += (double)part[(int64_t)c * n_out + o];
-    if (outf) outf[o] = (float)s;
-    if (outd) outd[o] = s;
+    for (int c = lane; c < nchunks; c += 32) s += (double)part[(int64_t)c * n_out + o];
+    s = warp_sum_d(s);
+    if (lane == 0) {
+        if (outf) outf[o] = (float)s;
+        if (outd) outd[o] = s;
+    }
 }
 
 // out(i, j) = sum_q U(i, q) Y(q, j): one warp per row, lanes over columns j (and j + 32)
@@ -162,7 +167,7 @@ static cudaError_t project(const float* U, int64_t n, int rp, const float* A, in
     const int64_t nc = proj_chunks(n);
     k_project<<<(unsigned)nc, kProjThreads, 0, st>>>(U, n, rp, A, r, part);
     count_launch();
-    k_project_sum<<<grid_of((int64_t)rp * r, 256), 256, 0, st>>>(part, (int)nc, rp * r, Wf, Wd);
+    k_project_sum<<<grid_of((int64_t)rp * r * 32, 256), 256, 0, st>>>(part, (int)nc, rp * r, Wf, Wd);
     count_launch();
     return cudaGetLastError();
 }
