@@ -31,8 +31,9 @@ struct MttkrpPlan {
     int RPH;             // tc: rank rounded up to 8 (B operand holds hi | lo, N = 2 RPH)
     int mode, rank, RP, R, n_pb;
     int I_T, O_T;
-    int64_t nb, n_ot, n_tiles;
+    int64_t nb, n_ot, n_tiles;   // row tiles
     int n_kc;
+    int n_cs = 1, kc_per = 0;    // tensor-core row kernels: column segments per row tile, chunks per segment
     int G;               // streaming CTAs along the tile axis
     int n_cb;            // last mode: 64-column blocks
     int Smax;

@@ -161,6 +161,11 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     const int cb_cols = P.tc ? 128 : kStageCols;
     P.n_cb = (int)ceil_div(v.C, cb_cols);
     P.Cpad = (int64_t)P.n_cb * cb_cols;
+    // tensor-core row kernels take tiles at run time and keep one slot per tile; the
+    // others own contiguous tile ranges and keep one slot per (CTA, segment)
+    P.tile_slots = P.tc && P.kind != ModeKind::Last;
+    P.n_cs = 1;
+    P.kc_per = P.n_kc;
     if (P.kind == ModeKind::Last) {
         int gs = sms / P.n_cb;
         if (gs < 1) gs = 1;
@@ -168,11 +173,18 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
         P.G = gs;
     } else {
         const int per_sm = (P.tc && !P.tf32 && 2 * tc_rows_smem(P.RPH) <= 227 * 1024) ? 2 : 1;
-        P.G = (int)std::min<int64_t>(P.n_tiles, (int64_t)sms * per_sm);
+        const int64_t cap = (int64_t)sms * per_sm;
+        if (P.tile_slots && P.n_tiles < 2 * cap && P.n_kc >= 8) {
+            // Few row tiles with long rows (e.g. merged modes): split each row tile into column
+            // segments of at least 4 chunks so that every CTA gets about two tiles to stream
+            const int64_t want = ceil_div(2 * cap, P.n_tiles);
+            const int64_t most = P.n_kc / 4;
+            const int64_t ncs = std::max<int64_t>(1, std::min(want, most));
+            P.kc_per = (int)ceil_div(P.n_kc, ncs);
+            P.n_cs = (int)ceil_div(P.n_kc, P.kc_per);     // no empty segment
+        }
+        P.G = (int)std::min<int64_t>(P.n_tiles * P.n_cs, cap);
     }
-    // tensor-core row kernels take tiles at run time and keep one slot per tile; the
-    // others own contiguous tile ranges and keep one slot per (CTA, segment)
-    P.tile_slots = P.tc && P.kind != ModeKind::Last;
     P.Smax = 1;
     if (P.kind == ModeKind::Inner && !P.tile_slots) {
         for (int g = 0; g < P.G; ++g) {
@@ -198,10 +210,10 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     P.off_part = off;
     size_t part = 0;
     if (P.kind == ModeKind::Inner)
-        part = P.tile_slots ? (size_t)P.n_tiles * P.I_T * P.RP
+        part = P.tile_slots ? (size_t)P.n_tiles * P.n_cs * P.I_T * P.RP
                             : (size_t)P.G * P.Smax * kStreamWarps * P.I_T * P.RP;
     else if (P.kind == ModeKind::Outer)
-        part = (size_t)v.n_o * P.nb * P.RP;
+        part = (size_t)v.n_o * P.nb * P.n_cs * P.RP;
     else
         part = (size_t)P.G * P.Cpad * P.RP;
     off = align256(off + sizeof(float) * part);
@@ -385,6 +397,11 @@ ReduceParams make_reduce_params(const TensorView& v, const MttkrpPlan& P, const 
     R.tile_slots = P.tile_slots ? 1 : 0;
     R.part = part;
     R.W = W;
+    if (P.tile_slots) {
+        // one slot per scheduled tile: a row tile's column segments are consecutive slots
+        if (P.kind == ModeKind::Inner) R.n_ot = P.n_ot * P.n_cs;
+        if (P.kind == ModeKind::Outer) R.nb = P.nb * P.n_cs;
+    }
     if (P.kind == ModeKind::Outer) {
         R.In = v.dims[P.mode];
         int64_t stride = 1;
@@ -469,8 +486,10 @@ ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* wor
         T.O_T = P.O_T;
         T.nb = P.nb;
         T.n_ot = P.n_ot;
-        T.n_tiles = P.n_tiles;
+        T.n_tiles = P.n_tiles * P.n_cs;
         T.n_kc = P.n_kc;
+        T.n_cs = P.n_cs;
+        T.kc_per = P.kc_per;
         T.sched = P.tile_slots ? reinterpret_cast<unsigned int*>(ws + P.off_sched) : nullptr;
         T.RP = P.RP;
         T.r = P.rank;

@@ -146,6 +146,18 @@ __device__ __forceinline__ void tile_coords(const TcParams& P, int64_t t, int64_
     else { ot = t / P.nb; ib = t % P.nb; }
 }
 
+// A scheduled tile t is row tile t / n_cs restricted to its column segment t % n_cs: the
+// chunks [kc0, kc1).  With one segment (the usual case) it is the whole row tile.  Every
+// scheduled tile has its own output slot, so the segments' partial sums meet only in the
+// fixed-order reduction.
+__device__ __forceinline__ void tile_chunks(const TcParams& P, int64_t t, int64_t& tb, int& kc0, int& kc1) {
+    const int ncs = P.n_cs > 0 ? P.n_cs : 1;
+    const int per = P.kc_per > 0 ? P.kc_per : P.n_kc;
+    tb = t / ncs;
+    kc0 = (int)(t - tb * ncs) * per;
+    kc1 = kc0 + per < P.n_kc ? kc0 + per : P.n_kc;
+}
+
 // the statically assigned first tile of this CTA (-1 if there is none)
 __device__ __forceinline__ int g_first_tile(int64_t n_tiles) {
     return (int64_t)blockIdx.x < n_tiles ? (int)blockIdx.x : -1;
@@ -200,15 +212,19 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
     // be in flight while the kernel before this one finishes (the packed factor chunks,
     // which that kernel writes, follow after the wait)
     const int first_tile = g_first_tile(P.n_tiles);
-    const int npre = first_tile >= 0 ? (P.n_kc < kTcStages ? P.n_kc : kTcStages) : 0;
+    int64_t ftb = 0;
+    int fkc0 = 0, fkc1 = 0;
+    if (first_tile >= 0) tile_chunks(P, first_tile, ftb, fkc0, fkc1);
+    const int npre = first_tile >= 0 ? (fkc1 - fkc0 < kTcStages ? fkc1 - fkc0 : kTcStages) : 0;
     if (warp == 4 && lane == 0) {
         prefetch_tensormap(&tmap);
         if (first_tile >= 0) {
             int64_t ib, ot;
-            tile_coords<INNER>(P, first_tile, ib, ot);
-            for (int kc = 0; kc < npre; ++kc) {
-                mbar_arrive_expect_tx(&full[kc], (uint32_t)kStage);
-                tma_load_3d(base_ptr + kc * kStage, &tmap, &full[kc], kc * 64, (int)(ib * P.I_T), (int)(ot * P.O_T));
+            tile_coords<INNER>(P, ftb, ib, ot);
+            for (int j = 0; j < npre; ++j) {
+                mbar_arrive_expect_tx(&full[j], (uint32_t)kStage);
+                tma_load_3d(base_ptr + j * kStage, &tmap, &full[j], (fkc0 + j) * 64, (int)(ib * P.I_T),
+                            (int)(ot * P.O_T));
             }
         }
     }
@@ -241,12 +257,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
                 tile_ring[slot] = t;
                 mbar_arrive(&sfull[slot]);              // releases the slot to the consumers
                 if (t < 0) break;
-                int64_t ib, ot;
-                tile_coords<INNER>(P, t, ib, ot);
+                int64_t ib, ot, tb;
+                int kc0, kc1;
+                tile_chunks(P, t, tb, kc0, kc1);
+                tile_coords<INNER>(P, tb, ib, ot);
                 bool ok = true;
-                for (int kc = 0; kc < P.n_kc; ++kc) {
+                for (int kc = kc0; kc < kc1; ++kc) {
                     unsigned char* st = base_ptr + stage * kStage;
-                    if (s == 0 && kc < npre) {
+                    if (s == 0 && kc - kc0 < npre) {
                         // stage kc already holds (or is receiving) this chunk of the tensor
                         bulk_load(st + kBoxBytes, FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
                     } else {
@@ -286,7 +304,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
             __syncwarp();
             if (lane == 0) mbar_arrive(&sempty[slot]);
             if (t < 0) break;
-            for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
+            int64_t tb;
+            int kc0, kc1;
+            tile_chunks(P, t, tb, kc0, kc1);
+            for (int kc = kc0; kc < kc1; ++kc, ++gq) {
                 const int d = (int)(gq % kDbuf);
                 if (!warp_wait(&tempty[d], (uint32_t)((gq / kDbuf) & 1) ^ 1u) || !warp_wait(&full[stage], phase)) {
                     if (lane == 0) record_device_error(P.err, kErrWaitFull);
@@ -337,8 +358,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
         __syncwarp();
         if (lane == 0) mbar_arrive(&sempty[slot]);
         if (t < 0) break;
-        int64_t ib, ot;
-        tile_coords<INNER>(P, t, ib, ot);
+        int64_t ib, ot, tb;
+        int kc0, kc1;
+        tile_chunks(P, t, tb, kc0, kc1);
+        tile_coords<INNER>(P, tb, ib, ot);
         // weights of this row, fetched while the tile is being contracted
         float w[RPH];
         bool row_live;
@@ -359,7 +382,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
         float y[RPH];
 #pragma unroll
         for (int p = 0; p < RPH; ++p) y[p] = 0.f;
-        for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
+        for (int kc = kc0; kc < kc1; ++kc, ++gq) {
             const int d = (int)(gq % kDbuf);
             if (ok && !warp_wait(&tfull[d], (uint32_t)((gq / kDbuf) & 1))) {
                 if (lane == 0) record_device_error(P.err, kErrWaitFull);
@@ -763,15 +786,19 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
     const uint32_t tmem = *tmem_slot;
     // CTA g's first tile is tile g; its first tensor boxes go out before the wait
     const int first_tile = g_first_tile(P.n_tiles);
-    const int npre = first_tile >= 0 ? (P.n_kc < kTfRaw ? P.n_kc : kTfRaw) : 0;
+    int64_t ftb = 0;
+    int fkc0 = 0, fkc1 = 0;
+    if (first_tile >= 0) tile_chunks(P, first_tile, ftb, fkc0, fkc1);
+    const int npre = first_tile >= 0 ? (fkc1 - fkc0 < kTfRaw ? fkc1 - fkc0 : kTfRaw) : 0;
     if (warp == 4 && lane == 0) {
         prefetch_tensormap(&tmap);
         if (first_tile >= 0) {
             int64_t ib, ot;
-            tile_coords<INNER>(P, first_tile, ib, ot);
-            for (int kc = 0; kc < npre; ++kc) {
-                mbar_arrive_expect_tx(&rfull[kc], (uint32_t)kTfBox);
-                tma_load_3d(boxes + kc * kTfBox, &tmap, &rfull[kc], kc * 32, (int)(ib * P.I_T), (int)(ot * P.O_T));
+            tile_coords<INNER>(P, ftb, ib, ot);
+            for (int j = 0; j < npre; ++j) {
+                mbar_arrive_expect_tx(&rfull[j], (uint32_t)kTfBox);
+                tma_load_3d(boxes + j * kTfBox, &tmap, &rfull[j], (fkc0 + j) * 32, (int)(ib * P.I_T),
+                            (int)(ot * P.O_T));
             }
         }
     }
@@ -793,7 +820,10 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
                 const int t = tile_ring[slot];
                 mbar_arrive(&sempty[slot]);
                 if (t < 0) break;
-                for (int kc = 0; kc < P.n_kc; ++kc, ++g) {
+                int64_t tb;
+                int kc0, kc1;
+                tile_chunks(P, t, tb, kc0, kc1);
+                for (int kc = kc0; kc < kc1; ++kc, ++g) {
                     const int bs = (int)(g % kTfB);
                     if (!mbar_wait_bounded(&bempty[bs], (uint32_t)((g / kTfB) & 1) ^ 1u)) {
                         record_device_error(P.err, kErrWaitEmpty);
@@ -830,10 +860,12 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
                 tile_ring[slot] = t;
                 mbar_arrive(&sfull[slot]);
                 if (t < 0) break;
-                int64_t ib, ot;
-                tile_coords<INNER>(P, t, ib, ot);
-                for (int kc = 0; kc < P.n_kc; ++kc, ++g) {
-                    if (!(s == 0 && kc < npre)) {
+                int64_t ib, ot, tb;
+                int kc0, kc1;
+                tile_chunks(P, t, tb, kc0, kc1);
+                tile_coords<INNER>(P, tb, ib, ot);
+                for (int kc = kc0; kc < kc1; ++kc, ++g) {
+                    if (!(s == 0 && kc - kc0 < npre)) {
                         const int rs = (int)(g % kTfRaw);
                         if (!mbar_wait_bounded(&rempty[rs], (uint32_t)((g / kTfRaw) & 1) ^ 1u)) {
                             record_device_error(P.err, kErrWaitEmpty);
@@ -873,7 +905,10 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
             __syncwarp();
             if (lane == 0) mbar_arrive(&sempty[slot]);
             if (t < 0) break;
-            for (int kc = 0; kc < P.n_kc; ++kc, ++g) {
+            int64_t tb;
+            int kc0, kc1;
+            tile_chunks(P, t, tb, kc0, kc1);
+            for (int kc = kc0; kc < kc1; ++kc, ++g) {
                 if ((int)(g % kTfConvGroups) != cg) continue;
                 const int rs = (int)(g % kTfRaw);
                 if (!warp_wait(&rfull[rs], (uint32_t)((g / kTfRaw) & 1))) {
@@ -939,7 +974,10 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
             __syncwarp();
             if (lane == 0) mbar_arrive(&sempty[slot]);
             if (t < 0) break;
-            for (int kc = 0; kc < P.n_kc; ++kc, ++g) {
+            int64_t tb;
+            int kc0, kc1;
+            tile_chunks(P, t, tb, kc0, kc1);
+            for (int kc = kc0; kc < kc1; ++kc, ++g) {
                 if ((int)(g & 1) != mg) continue;
                 const int d = (int)(g % kTfDbuf), a = (int)(g % kTfA), bs = (int)(g % kTfB);
                 if (!warp_wait(&tempty[d], (uint32_t)((g / kTfDbuf) & 1) ^ 1u) ||
@@ -995,8 +1033,10 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
         __syncwarp();
         if (lane == 0) mbar_arrive(&sempty[slot]);
         if (t < 0) break;
-        int64_t ib, ot;
-        tile_coords<INNER>(P, t, ib, ot);
+        int64_t ib, ot, tb;
+        int kc0, kc1;
+        tile_chunks(P, t, tb, kc0, kc1);
+        tile_coords<INNER>(P, tb, ib, ot);
         float w[RPH];
         bool row_live;
         if (INNER) {
@@ -1015,7 +1055,7 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
         float y[RPH];
 #pragma unroll
         for (int p = 0; p < RPH; ++p) y[p] = 0.f;
-        for (int kc = 0; kc < P.n_kc; ++kc, ++gq) {
+        for (int kc = kc0; kc < kc1; ++kc, ++gq) {
             const int d = (int)(gq % kTfDbuf);
             if (ok && !warp_wait(&tfull[d], (uint32_t)((gq / kTfDbuf) & 1))) {
                 if (lane == 0) record_device_error(P.err, kErrWaitFull);

@@ -10,8 +10,9 @@ namespace ntf {
 struct TcParams {
     int64_t C, Ii, n_o;
     int I_T, O_T;
-    int64_t nb, n_ot, n_tiles;
+    int64_t nb, n_ot, n_tiles;      // n_tiles: scheduled tiles (row tiles x column segments)
     int n_kc;
+    int n_cs, kc_per;                // column segments per row tile, chunks per segment
     int RP, r;
     int Smax;
     int64_t Cpad;

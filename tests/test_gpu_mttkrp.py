@@ -31,6 +31,9 @@ SHAPES = [
     ((150, 1000, 50), 25),
     ((50, 50, 50), 10),       # the paper's cube
     ((1, 200, 1), 4),
+    ((8, 16, 2048), 16),      # few row tiles, long rows: column segments per row tile
+    ((4, 3, 4096), 20),       # ... with ragged rows and the tensor-core rank limit below
+    ((6, 40, 1536), 32),
 ]
 
 
