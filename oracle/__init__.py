@@ -68,7 +68,7 @@ def _load():
             lib.oracle_her_decide.argtypes = [_D, C.c_double, C.c_double, C.c_double, C.c_double]
             tail = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
                     C.c_double, C.c_double, C.c_double, C.c_double,
-                    _D, _D, _D, C.POINTER(C.c_int), _D, _D, _D, _D]
+                    _D, _D, _D, C.POINTER(C.c_int), _D, _D, _D, _D, C.POINTER(C.c_int)]
             lib.oracle_solve.argtypes = [C.c_int, _I64, _D, C.POINTER(_D), C.c_int] + tail
             lib.oracle_solve_tucker.argtypes = [C.c_int, _I64, _I64, _D, C.POINTER(_D), C.POINTER(_D),
                                                 C.c_int] + tail
@@ -298,8 +298,12 @@ _METHODS = {"hals": 0, "pgd": 1, "nesterov": 2}
 
 
 def _solve_common(fn, prefix, dims, init, iters, her, method, inner_max, inner_tol, beta0, gamma,
-                  gamma_bar, eta, track_true, track_blocks, track_factors):
+                  gamma_bar, eta, track_true, track_blocks, track_factors, force=None):
     F = [_f64(A).copy() for A in init]
+    if force is not None:
+        force = np.ascontiguousarray(force, dtype=np.int32)
+        if force.shape != (iters,):
+            raise ValueError("force needs one entry per iteration")
     r = F[0].shape[1]
     tr = SolveTrace(iters, dims, r, track_factors)
     rc = fn(*prefix, _ptr_array(F), r, int(her), _METHODS[method], inner_max, inner_tol, iters,
@@ -309,7 +313,8 @@ def _solve_common(fn, prefix, dims, init, iters, her, method, inner_max, inner_t
             _ptr(tr.ftrue) if track_true else None,
             _ptr(tr.fblock) if track_blocks else None,
             _ptr(tr.fhat0),
-            _ptr(tr._fac) if track_factors else None)
+            _ptr(tr._fac) if track_factors else None,
+            force.ctypes.data_as(C.POINTER(C.c_int)) if force is not None else None)
     if rc:
         raise ValueError("oracle solve: bad arguments")
     return F, tr
@@ -318,9 +323,10 @@ def _solve_common(fn, prefix, dims, init, iters, her, method, inner_max, inner_t
 def solve(T, init, iters: int, her: bool = True, method: str = "hals", inner_max: int = 1,
           inner_tol: float = 1e-2, beta0: float = 0.5, gamma: float = 1.05,
           gamma_bar: float = 1.01, eta: float = 1.5, track_true: bool = False,
-          track_blocks: bool = False, track_factors: bool = False):
+          track_blocks: bool = False, track_factors: bool = False, force=None):
     """Alg. 1 (``her=False``) or Alg. 2 (``her=True``) in FP64 from ``init``.
-    ``method`` is "hals", "pgd" or "nesterov".
+    ``method`` is "hals", "pgd" or "nesterov".  ``force``: optional per-iteration -1 / 0 / 1
+    (take Alg. 2's accept or restart branch at that iteration whatever F-hat says).
 
     Returns ``(factors, trace)``; ``trace.fhat[k-1]`` is F-hat_k (the value Alg. 2's restart test compares),
     ``trace.ftrue[k-1]`` the explicit objective at A_k when ``track_true``; with ``track_factors``
@@ -331,7 +337,7 @@ def solve(T, init, iters: int, her: bool = True, method: str = "hals", inner_max
     d, dp = _dims(T)
     return _solve_common(lib.oracle_solve, (T.ndim, dp, _ptr(T)), T.shape, init, iters, her, method,
                          inner_max, inner_tol, beta0, gamma, gamma_bar, eta, track_true, track_blocks,
-                         track_factors)
+                         track_factors, force)
 
 
 # --- Tucker-format data (Appendix A) -----------------------------------------
@@ -381,11 +387,11 @@ def tucker_norm_sq(G, U) -> float:
 def solve_tucker(G, U, init, iters: int, her: bool = True, method: str = "hals", inner_max: int = 1,
                  inner_tol: float = 1e-2, beta0: float = 0.5, gamma: float = 1.05,
                  gamma_bar: float = 1.01, eta: float = 1.5, track_true: bool = False,
-                 track_blocks: bool = False, track_factors: bool = False):
+                 track_blocks: bool = False, track_factors: bool = False, force=None):
     """Alg. 1 / Alg. 2 on the Tucker-format objective F_t of Appendix A (eq. objFunTucker)."""
     lib = _load()
     G, U, dims, cdims = _tucker_args(G, U)
     return _solve_common(lib.oracle_solve_tucker,
                          (G.ndim, dims.ctypes.data_as(_I64), cdims.ctypes.data_as(_I64), _ptr(G), _ptr_array(U)),
                          [int(x) for x in dims], init, iters, her, method, inner_max, inner_tol, beta0, gamma,
-                         gamma_bar, eta, track_true, track_blocks, track_factors)
+                         gamma_bar, eta, track_true, track_blocks, track_factors, force)

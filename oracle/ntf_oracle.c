@@ -605,12 +605,17 @@ static double data_objective(const data_term* D, int order, const int64_t* dims,
  *                     factors A^l_k right after the block updates, the
  *                     extrapolated A_hat^l_k before the decision, and A^l_k
  *                     after the decision, each mode after mode.
+ * force (may be NULL): per iteration -1, or 0 / 1 to take the accept / restart
+ * branch of Alg. 2 whatever the comparison of F-hat says (used by the tests to
+ * follow a run that decided a tie the other way; the branch itself, its beta
+ * updates and F-hat_{k-1} <- F-hat_k are Alg. 2's).
  * A holds the initial factors on entry and the final A_k on exit. */
 static int solve_impl(const data_term* D, int order, const int64_t* dims, double* const* A, int r,
                       int her, int method, int inner_max, double inner_tol, int max_iters,
                       double beta0, double gamma, double gamma_bar, double eta,
                       double* out_fhat, double* out_beta, double* out_beta_bar, int* out_restart,
-                      double* out_ftrue, double* out_fblock, double* out_fhat0, double* out_factors) {
+                      double* out_ftrue, double* out_fblock, double* out_fhat0, double* out_factors,
+                      const int* force) {
     if (check_shape(order, dims, r) || inner_max < 1 || max_iters < 0) return -1;
     const double tnorm = D->U ? oracle_tucker_norm_sq(order, dims, D->cdims, D->T, D->U)
                               : oracle_norm_sq(D->T, numel_of(order, dims));
@@ -670,7 +675,10 @@ static int solve_impl(const data_term* D, int order, const int64_t* dims, double
         const double fhat = oracle_objective_identity(tnorm, M[last], A[last], dims[last], r, V);
         int restart = 0;
         if (her) {
-            restart = oracle_her_decide(state, fhat, gamma, gamma_bar, eta);
+            const int f = force ? force[k - 1] : -1;
+            /* a forced branch compares an infinite F-hat, then records the real one */
+            restart = oracle_her_decide(state, f < 0 ? fhat : (f ? INFINITY : -INFINITY), gamma, gamma_bar, eta);
+            state[2] = fhat;
             for (int l = 0; l < order; ++l) {
                 const size_t bytes = sizeof(double) * (size_t)dims[l] * (size_t)r;
                 if (restart) memcpy(Ahat[l], A[l], bytes);   /* abandon A_hat */
@@ -704,11 +712,12 @@ int oracle_solve(int order, const int64_t* dims, const double* T, double* const*
                  int her, int method, int inner_max, double inner_tol, int max_iters,
                  double beta0, double gamma, double gamma_bar, double eta,
                  double* out_fhat, double* out_beta, double* out_beta_bar, int* out_restart,
-                 double* out_ftrue, double* out_fblock, double* out_fhat0, double* out_factors) {
+                 double* out_ftrue, double* out_fblock, double* out_fhat0, double* out_factors,
+                 const int* force) {
     const data_term D = {T, NULL, NULL};
     return solve_impl(&D, order, dims, A, r, her, method, inner_max, inner_tol, max_iters, beta0, gamma,
                       gamma_bar, eta, out_fhat, out_beta, out_beta_bar, out_restart, out_ftrue, out_fblock,
-                      out_fhat0, out_factors);
+                      out_fhat0, out_factors, force);
 }
 
 /* Alg. 1 / Alg. 2 on the Tucker-format objective F_t of Appendix A (eq.
@@ -719,12 +728,13 @@ int oracle_solve_tucker(int order, const int64_t* dims, const int64_t* cdims, co
                         int her, int method, int inner_max, double inner_tol, int max_iters,
                         double beta0, double gamma, double gamma_bar, double eta,
                         double* out_fhat, double* out_beta, double* out_beta_bar, int* out_restart,
-                        double* out_ftrue, double* out_fblock, double* out_fhat0, double* out_factors) {
+                        double* out_ftrue, double* out_fblock, double* out_fhat0, double* out_factors,
+                        const int* force) {
     if (!cdims || !U || check_shape(order, cdims, 1)) return -1;
     const data_term D = {G, cdims, U};
     return solve_impl(&D, order, dims, A, r, her, method, inner_max, inner_tol, max_iters, beta0, gamma,
                       gamma_bar, eta, out_fhat, out_beta, out_beta_bar, out_restart, out_ftrue, out_fblock,
-                      out_fhat0, out_factors);
+                      out_fhat0, out_factors, force);
 }
 
 /* ------------------------------------------------------------------------ */

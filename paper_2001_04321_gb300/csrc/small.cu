@@ -15,79 +15,132 @@ namespace ntf {
 
 
 // ---------------------------------------------------------------------------
-// a2: Gram A^T A (one CTA; FP32 over 32-row blocks, FP64 across blocks)
+// a2: Gram A^T A.  Rows are staged in shared memory in blocks (zero-padded to 4T columns,
+// T = ceil(r / 4)).  Thread (tp, grp) owns the 4 x 4 tile pair tp = (a, b), a <= b, of the upper
+// triangle and rows grp, grp + ngrp, ... of the block (at most 32 of them): 16 FP32 accumulators,
+// two 16-byte shared loads per row.  The ngrp row groups are then added per entry in FP64 in
+// group order, and the blocks in FP64 in block order.  Deterministic, no workspace.
 // ---------------------------------------------------------------------------
-constexpr int kGramThreads = 512;
-constexpr int kGramChunk = 128;   // rows staged in shared memory at a time
+constexpr int kGramThreads = 1024;
 
-// Accumulates the upper triangle of A^T A into acc[] (pairs t, t+512, ...);
-// sA has room for kGramChunk * r floats.
-__device__ void gram_accumulate(const float* __restrict__ A, int64_t rows, int r, float* sA, double acc[5]) {
-    const int npairs = r * (r + 1) / 2;
-    for (int64_t r0 = 0; r0 < rows; r0 += kGramChunk) {
-        const int nrow = (int)(rows - r0 < kGramChunk ? rows - r0 : kGramChunk);
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < nrow * r; idx += blockDim.x) sA[idx] = A[r0 * r + idx];
-        __syncthreads();
-        int k = 0;
-        for (int q = threadIdx.x; q < npairs; q += blockDim.x, ++k) {
-            // pair index -> (p, c) with p <= c
-            int p = 0, rem = q;
-            while (rem >= r - p) { rem -= r - p; ++p; }
-            const int c = p + rem;
-            for (int b0 = 0; b0 < nrow; b0 += 32) {
-                const int b1 = min(nrow, b0 + 32);
-                float s = 0.f;
-                for (int i = b0; i < b1; ++i) s = fmaf(sA[i * r + p], sA[i * r + c], s);
-                acc[k] += (double)s;
-            }
+__host__ __device__ __forceinline__ int gram_tiles(int r) { return (r + 3) / 4; }
+__host__ __device__ __forceinline__ int gram_tile_pairs(int r) { return gram_tiles(r) * (gram_tiles(r) + 1) / 2; }
+__host__ __device__ __forceinline__ int gram_groups(int r) {
+    const int g = kGramThreads / gram_tile_pairs(r);
+    return g < 1 ? 1 : g;
+}
+// rows of one staged block: at most 32 per row group
+__host__ __device__ __forceinline__ int gram_blk_rows(int r) {
+    const int b = gram_groups(r) * 32;
+    return b > 1024 ? 1024 : b;
+}
+__host__ __device__ __forceinline__ int gram_stride(int r) { return 4 * gram_tiles(r) + 4; }
+
+__device__ __forceinline__ void pair_of(int q, int r, int& p, int& c) {
+    p = 0;
+    int rem = q;
+    while (rem >= r - p) {
+        rem -= r - p;
+        ++p;
+    }
+    c = p + rem;
+}
+
+// acc[q] += entry q (upper triangle, row-major pair order) of the Gram of rows [r0, r0 + n) of
+// A, n <= gram_blk_rows(r); sA holds max(n * stride, ngrp * ntp * 16) floats
+__device__ void gram_chunk(const float* __restrict__ A, int64_t r0, int n, int r, float* sA, double* acc) {
+    const int T = gram_tiles(r), S = gram_stride(r), ntp = gram_tile_pairs(r), ngrp = gram_groups(r);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * S; t += blockDim.x) {
+        const int i = t / S, j = t - i * S;
+        sA[t] = j < r ? A[(r0 + i) * r + j] : 0.f;
+    }
+    __syncthreads();
+    const int tid = threadIdx.x;
+    float x16[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) x16[e] = 0.f;
+    const bool active = tid < ntp * ngrp;
+    const int tp = tid % ntp, grp = tid / ntp;
+    if (active) {
+        int a, b;
+        pair_of(tp, T, a, b);
+        for (int i = grp; i < n; i += ngrp) {
+            const float4 u = *reinterpret_cast<const float4*>(sA + i * S + 4 * a);
+            const float4 v = *reinterpret_cast<const float4*>(sA + i * S + 4 * b);
+            const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 16; ++e) x16[e] = fmaf(uu[e >> 2], vv[e & 3], x16[e]);
         }
+    }
+    __syncthreads();                       // sA is reused for the row-group partials
+    if (active)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) sA[(grp * ntp + tp) * 16 + e] = x16[e];
+    __syncthreads();
+    for (int idx = tid; idx < ntp * 16; idx += blockDim.x) {
+        const int t2 = idx >> 4, e = idx & 15;
+        int a, b;
+        pair_of(t2, T, a, b);
+        const int p = 4 * a + (e >> 2), c = 4 * b + (e & 3);
+        if (p >= r || c >= r || p > c) continue;
+        double s = 0.0;
+        for (int g0 = 0; g0 < ngrp; g0 += 16) {          // FP32 over 16 groups, FP64 across
+            float f = 0.f;
+            const int g1 = g0 + 16 < ngrp ? g0 + 16 : ngrp;
+            for (int g = g0; g < g1; ++g) f += sA[(g * ntp + t2) * 16 + e];
+            s += (double)f;
+        }
+        acc[p * r - p * (p - 1) / 2 + (c - p)] += s;
     }
 }
 
-__device__ void gram_store(int r, const double acc[5], double* G) {
+// shared memory of the Gram kernels: 2080 FP64 entries (r = 64) and the staged block / partials
+size_t gram_smem(int r) {
+    const size_t stage = (size_t)gram_blk_rows(r) * gram_stride(r);
+    const size_t red = (size_t)gram_groups(r) * gram_tile_pairs(r) * 16;
+    return sizeof(double) * 2080 + sizeof(float) * (stage > red ? stage : red);
+}
+
+// the whole Gram in one CTA (any number of rows)
+__device__ void gram_cta(const float* __restrict__ A, int64_t rows, int r, float* sA, double* acc) {
     const int npairs = r * (r + 1) / 2;
-    int k = 0;
-    for (int q = threadIdx.x; q < npairs; q += blockDim.x, ++k) {
-        int p = 0, rem = q;
-        while (rem >= r - p) { rem -= r - p; ++p; }
-        const int c = p + rem;
-        G[p * r + c] = acc[k];
-        G[c * r + p] = acc[k];
-    }
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x) acc[q] = 0.0;
+    const int blk = gram_blk_rows(r);
+    for (int64_t r0 = 0; r0 < rows; r0 += blk) gram_chunk(A, r0, (int)(rows - r0 < blk ? rows - r0 : blk), r, sA, acc);
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(kGramThreads) k_gram(const float* __restrict__ A, int64_t rows, int r,
                                                        double* __restrict__ G) {
-    extern __shared__ float sA[];
-    double acc[5] = {0, 0, 0, 0, 0};
-    gram_accumulate(A, rows, r, sA, acc);
-    gram_store(r, acc, G);
+    extern __shared__ __align__(16) unsigned char gram_smem_raw[];
+    double* acc = reinterpret_cast<double*>(gram_smem_raw);
+    float* sA = reinterpret_cast<float*>(gram_smem_raw + sizeof(double) * 2080);
+    gram_cta(A, rows, r, sA, acc);
+    const int npairs = r * (r + 1) / 2;
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+        int p, c;
+        pair_of(q, r, p, c);
+        G[p * r + c] = acc[q];
+        G[c * r + p] = acc[q];
+    }
 }
 
-size_t gram_smem(int r) { return sizeof(float) * kGramChunk * r; }
 
-cudaError_t launch_gram(const float* A, int64_t rows, int r, double* G, cudaStream_t st) {
-    k_gram<<<1, kGramThreads, gram_smem(r), st>>>(A, rows, r, G);
-    count_launch();
-    return cudaGetLastError();
-}
-
-// Many-row Grams: each CTA accumulates kGramBlkRows rows as k_gram does (FP32 over 32-row
-// blocks, FP64 across them) into its own slot of upper-triangle partials; k_gram_sum adds the
-// slots in CTA order.  Deterministic, like the one-CTA kernel.
-constexpr int kGramBlkRows = 1024;
-
+// Many-row Grams: one CTA per row block writes its entries to its own slot of partials;
+// k_gram_sum adds the slots in block order.
 __global__ void __launch_bounds__(kGramThreads) k_gram_part(const float* __restrict__ A, int64_t rows, int r,
                                                             double* __restrict__ parts) {
-    extern __shared__ float sA[];
-    const int64_t r0 = (int64_t)blockIdx.x * kGramBlkRows;
-    const int64_t n = rows - r0 < kGramBlkRows ? rows - r0 : kGramBlkRows;
-    double acc[5] = {0, 0, 0, 0, 0};
-    gram_accumulate(A + r0 * r, n, r, sA, acc);
+    extern __shared__ __align__(16) unsigned char gram_smem_raw[];
+    double* acc = reinterpret_cast<double*>(gram_smem_raw);
+    float* sA = reinterpret_cast<float*>(gram_smem_raw + sizeof(double) * 2080);
+    const int blk = gram_blk_rows(r);
     const int npairs = r * (r + 1) / 2;
-    int k = 0;
-    for (int q = threadIdx.x; q < npairs; q += blockDim.x, ++k) parts[(int64_t)blockIdx.x * npairs + q] = acc[k];
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x) acc[q] = 0.0;
+    const int64_t r0 = (int64_t)blockIdx.x * blk;
+    gram_chunk(A, r0, (int)(rows - r0 < blk ? rows - r0 : blk), r, sA, acc);
+    __syncthreads();
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x) parts[(int64_t)blockIdx.x * npairs + q] = acc[q];
 }
 
 __global__ void k_gram_sum(const double* __restrict__ parts, int nblk, int r, double* __restrict__ G) {
@@ -96,20 +149,42 @@ __global__ void k_gram_sum(const double* __restrict__ parts, int nblk, int r, do
     if (q >= npairs) return;
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += parts[(int64_t)b * npairs + q];
-    int p = 0, rem = q;
-    while (rem >= r - p) { rem -= r - p; ++p; }
-    const int c = p + rem;
+    int p, c;
+    pair_of(q, r, p, c);
     G[p * r + c] = s;
     G[c * r + p] = s;
 }
 
+// the dynamic shared memory of the Gram and objective kernels (above 48 KB), set once
+static cudaError_t configure_gram_kernels() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    int bytes = 0;
+    for (int r = 1; r <= NTF_MAX_RANK; ++r) bytes = (int)gram_smem(r) > bytes ? (int)gram_smem(r) : bytes;
+    cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gram_part, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+cudaError_t launch_gram(const float* A, int64_t rows, int r, double* G, cudaStream_t st) {
+    cudaError_t e = configure_gram_kernels();
+    if (e != cudaSuccess) return e;
+    k_gram<<<1, kGramThreads, gram_smem(r), st>>>(A, rows, r, G);
+    count_launch();
+    return cudaGetLastError();
+}
+
 size_t gram_parts_bytes(int64_t rows, int r) {
-    return sizeof(double) * (size_t)((rows + kGramBlkRows - 1) / kGramBlkRows) * (size_t)(r * (r + 1) / 2);
+    return sizeof(double) * (size_t)((rows + gram_blk_rows(r) - 1) / gram_blk_rows(r)) * (size_t)(r * (r + 1) / 2);
 }
 
 cudaError_t launch_gram_parts(const float* A, int64_t rows, int r, double* G, double* parts, cudaStream_t st) {
-    if (!parts || rows <= kGramBlkRows) return launch_gram(A, rows, r, G, st);
-    const int nblk = (int)((rows + kGramBlkRows - 1) / kGramBlkRows);
+    const int blk = gram_blk_rows(r);
+    if (!parts || rows <= 2 * (int64_t)blk) return launch_gram(A, rows, r, G, st);
+    cudaError_t e = configure_gram_kernels();
+    if (e != cudaSuccess) return e;
+    const int nblk = (int)((rows + blk - 1) / blk);
     k_gram_part<<<nblk, kGramThreads, gram_smem(r), st>>>(A, rows, r, parts);
     count_launch();
     const int npairs = r * (r + 1) / 2;
@@ -145,22 +220,25 @@ __global__ void k_block_gradient(const float* __restrict__ A, int64_t rows, int 
     for (int q = threadIdx.x; q < r * r; q += blockDim.x) Vs[q] = (float)V[q];
     __syncthreads();
     const float sc = (float)(scale_dev ? *scale_dev * scale : scale);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows; i += (int64_t)gridDim.x * blockDim.x) {
+    // one thread per entry (i, j): g = sum_l A(i,l) V(l,j) - M(i,j); the threads of a row read
+    // A(i,:) together (broadcast) and consecutive columns of V
+    const int64_t n = rows * r;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / r;
+        const int j = (int)(idx - i * r);
         const float* a = A + i * r;
-        for (int j = 0; j < r; ++j) {
-            float g = -M[i * r + j];
-            for (int l = 0; l < r; ++l) g = fmaf(a[l], Vs[l * r + j], g);
-            out[i * r + j] = sc * g;
-        }
+        float g = -M[idx];
+        for (int l = 0; l < r; ++l) g = fmaf(a[l], Vs[l * r + j], g);
+        out[idx] = sc * g;
     }
 }
 
 cudaError_t launch_block_gradient(const float* A, int64_t rows, int r, const float* M, const double* V,
                                   const double* scale_dev, double scale, float* out, cudaStream_t st) {
-    int64_t g = (rows + 127) / 128;
+    int64_t g = (rows * r + 255) / 256;
     if (g > 1024) g = 1024;
     if (g < 1) g = 1;
-    k_block_gradient<<<(int)g, 128, 0, st>>>(A, rows, r, M, V, scale_dev, scale, out);
+    k_block_gradient<<<(int)g, 256, 0, st>>>(A, rows, r, M, V, scale_dev, scale, out);
     count_launch();
     return cudaGetLastError();
 }
@@ -217,46 +295,62 @@ cudaError_t launch_extrapolate(const float* A, const float* Ap, const double* be
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kGramThreads) k_objective(const double* __restrict__ tn, const float* __restrict__ M,
                                                             const float* __restrict__ A, int64_t rows, int r,
-                                                            const double* __restrict__ V, double* __restrict__ out,
-                                                            double* __restrict__ G_out) {
-    extern __shared__ __align__(16) unsigned char obj_smem[];
+                                                            const double* __restrict__ V, const double* __restrict__ G_in,
+                                                            double* __restrict__ out, double* __restrict__ G_out) {
+    extern __shared__ __align__(16) unsigned char gram_smem_raw[];
     __shared__ double sbuf[33];
-    double* Gs = reinterpret_cast<double*>(obj_smem);                    // r x r
-    float* sA = reinterpret_cast<float*>(obj_smem + sizeof(double) * r * r);  // kGramChunk x r
-    // <M, A>: FP32 products summed over at most 32 entries, then FP64
+    double* acc = reinterpret_cast<double*>(gram_smem_raw);
+    float* sA = reinterpret_cast<float*>(gram_smem_raw + sizeof(double) * 2080);
+    // <M, A>: thread t sums entries t, t + T, ... (coalesced), FP32 over 32 of them, then FP64
     const int64_t n = rows * r;
+    const int64_t T = blockDim.x;
     double inner = 0.0;
-    for (int64_t b = (int64_t)threadIdx.x * 32; b < n; b += (int64_t)blockDim.x * 32) {
+    for (int64_t b = threadIdx.x; b < n; b += 32 * T) {
         float s = 0.f;
-        const int64_t e = (n < b + 32) ? n : b + 32;
-        for (int64_t i = b; i < e; ++i) s = fmaf(M[i], A[i], s);
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const int64_t i = b + k * T;
+            if (i < n) s = fmaf(M[i], A[i], s);
+        }
         inner += (double)s;
     }
     inner = block_sum_d(inner, sbuf);
-    double acc[5] = {0, 0, 0, 0, 0};
-    gram_accumulate(A, rows, r, sA, acc);
-    __syncthreads();
-    gram_store(r, acc, Gs);
-    __syncthreads();
+    // sum_pq V(p,q) G(p,q), G = A^T A: given (the caller's Gram of A) or formed here
+    const int npairs = r * (r + 1) / 2;
     double quad = 0.0;
-    for (int q = threadIdx.x; q < r * r; q += blockDim.x) quad += V[q] * Gs[q];
+    if (G_in) {
+        for (int q = threadIdx.x; q < r * r; q += blockDim.x) quad += V[q] * G_in[q];
+    } else {
+        gram_cta(A, rows, r, sA, acc);
+        for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+            int p, c;
+            pair_of(q, r, p, c);
+            quad += (p == c ? V[p * r + p] : V[p * r + c] + V[c * r + p]) * acc[q];
+            if (G_out) {
+                G_out[p * r + c] = acc[q];
+                G_out[c * r + p] = acc[q];
+            }
+        }
+    }
     quad = block_sum_d(quad, sbuf);
     if (threadIdx.x == 0) *out = *tn - 2.0 * inner + quad;
-    if (G_out)
-        for (int q = threadIdx.x; q < r * r; q += blockDim.x) G_out[q] = Gs[q];
 }
 
 cudaError_t launch_objective(const double* tn, const float* M, const float* A, int64_t rows, int r, const double* V,
-                             double* out, double* G_out, cudaStream_t st) {
-    const size_t smem = sizeof(double) * r * r + gram_smem(r);
+                             double* out, double* G_out, cudaStream_t st, const double* G_in) {
+    const size_t smem = G_in ? 0 : gram_smem(r);
     static size_t set_bytes = 0;
-    if (set_bytes < smem) {
-        cudaError_t e = cudaFuncSetAttribute(k_objective, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (set_bytes == 0) {
+        size_t most = 0;
+        for (int q = 1; q <= NTF_MAX_RANK; ++q) most = gram_smem(q) > most ? gram_smem(q) : most;
+        cudaError_t e = cudaFuncSetAttribute(k_objective, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
         if (e != cudaSuccess) return e;
-        set_bytes = smem;
+        e = configure_gram_kernels();
+        if (e != cudaSuccess) return e;
+        set_bytes = most;
     }
     if (!M) return cudaSuccess;   // configuration only
-    k_objective<<<1, kGramThreads, smem, st>>>(tn, M, A, rows, r, V, out, G_out);
+    k_objective<<<1, kGramThreads, smem, st>>>(tn, M, A, rows, r, V, G_in, out, G_out);
     count_launch();
     return cudaGetLastError();
 }

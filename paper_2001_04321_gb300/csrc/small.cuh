@@ -40,7 +40,7 @@ cudaError_t launch_extrapolate(const float* A, const float* Ap, const double* be
 
 // out = *tn - 2<M,A> + sum(V (*) A^T A); optionally stores A^T A in G_out
 cudaError_t launch_objective(const double* tn, const float* M, const float* A, int64_t rows, int r, const double* V,
-                             double* out, double* G_out, cudaStream_t st);
+                             double* out, double* G_out, cudaStream_t st, const double* G_in = nullptr);
 
 int stream_red_blocks();
 cudaError_t launch_sum_parts(const double* parts, int n, double* out, cudaStream_t st);   // fixed order

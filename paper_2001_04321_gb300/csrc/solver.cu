@@ -477,7 +477,9 @@ struct Solver {
         }
         // F-hat_k = ||T||^2 - 2 <M_{N-1}, A_{N-1}> + sum(V_{N-1} (*) G(A_{N-1}))   (Alg. 2, restart test)
         const int last = N - 1;
-        cudaError_t e = launch_objective(&scal[0], M, A[last], vs.dims[last], r, V, &scal[1], nullptr, st);
+        // the Gram of A_{N-1} was just formed (into G with HER, else into Gh, the same factor)
+        cudaError_t e = launch_objective(&scal[0], M, A[last], vs.dims[last], r, V, &scal[1], nullptr, st,
+                                         use_her ? G[last] : Gh[last]);
         if (e != cudaSuccess) return cuda_fail(e, "objective");
         if (use_her) {
             CopyPairs P;
@@ -524,7 +526,7 @@ struct Solver {
             if (e != cudaSuccess) return cuda_fail(e, "hadamard");
             s = run_tucker_mttkrp(tk, tkp[N - 1], fac, Mrep, ws_tk, st, &tm[N - 1]);
             if (s != NTF_OK) return s;
-            e = launch_objective(&scal[0], Mrep, fac[N - 1], vu.dims[N - 1], r, Vrep, out, nullptr, st);
+            e = launch_objective(&scal[0], Mrep, fac[N - 1], vu.dims[N - 1], r, Vrep, out, nullptr, st, Grep[N - 1]);
             return e == cudaSuccess ? NTF_OK : cuda_fail(e, "objective");
         }
         const int RP = (int)round_up(r, 4);

@@ -55,3 +55,28 @@ def check_trajectory(fh, rs, tr, tnorm_sq, min_k, atol_rel=1e-6, f_true=None, f_
     if f_true is not None:
         assert abs(f_true - f_true_ref) <= 1e-3 * f_true_ref + atol, (f_true, f_true_ref, atol)
     return k
+
+
+def follow_trajectory(fh, rs, run_oracle, tnorm_sq, atol_rel=1e-6, max_ties=8):
+    """Trajectory parity that follows a tie.  ``run_oracle(force)`` runs the oracle with the
+    per-iteration forced decisions ``force`` (-1 = Alg. 2's own comparison) and returns
+    ``(factors, trace)``.  Wherever the solver decided differently from the oracle, the oracle's own
+    margin must be a tie below F-hat's resolution (2 atol, ``atol = atol_rel ||T||^2``); the oracle
+    is then rerun taking the solver's branch there, until every decision matches.  Then F-hat
+    agrees at every iteration.  Returns ``(factors, trace, ties)`` of the matching oracle run."""
+    atol = atol_rel * tnorm_sq
+    rs = np.asarray(rs)
+    fh = np.asarray(fh)
+    force = np.full(len(rs), -1, dtype=np.int32)
+    for _ in range(max_ties + 1):
+        F, tr = run_oracle(force)
+        diff = np.nonzero(rs != tr.restart)[0]
+        if diff.size == 0:
+            np.testing.assert_allclose(fh, tr.fhat, rtol=0, atol=atol)
+            return F, tr, int((force >= 0).sum())
+        k = int(diff[0])
+        np.testing.assert_allclose(fh[:k], tr.fhat[:k], rtol=0, atol=atol)
+        prev = tr.fhat[k - 1] if k > 0 else tr.fhat0[0]
+        assert abs(tr.fhat[k] - prev) <= 2 * atol, f"decision {k + 1} differs away from a tie"
+        force[k] = rs[k]
+    raise AssertionError(f"more than {max_ties} ties")

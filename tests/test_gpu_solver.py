@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_helpers import check_trajectory, device_tensor, rel_fro
+from gpu_helpers import check_trajectory, device_tensor, follow_trajectory, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -79,9 +79,14 @@ def test_solver_ahals_inner_loop():
     T, init, buf, d, ld, Fd = _setup(dims, r, 1e-2, 91)
     opts = ntf.Opts(max_iters=iters, inner_max=50, inner_tol=1e-2)
     fh, rs, rep = _trajectory(buf, d, ld, [A.clone() for A in Fd], iters, opts)
-    _, tr = oracle.solve(T, init, iters, her=True, inner_max=50, inner_tol=1e-2, track_true=True)
-    # this trajectory has a near-tie at iteration 14 (F_14 - F_13 = -8e-8 ||T||^2)
-    _check_trajectory(fh, rs, tr, oracle.norm_sq(T), 10, f_true=rep.f_true_last, f_true_ref=tr.ftrue[-1])
+    # this trajectory has a near-tie at iteration 14 (F_14 - F_13 = -8e-8 ||T||^2) that rounding
+    # decides either way: the oracle follows the solver's branch there, and then every F-hat
+    # and the final objective agree
+    run = lambda force: oracle.solve(T, init, iters, her=True, inner_max=50, inner_tol=1e-2, track_true=True,
+                                     force=force)
+    _, tr, ties = follow_trajectory(fh, rs, run, oracle.norm_sq(T))
+    assert ties <= 2
+    assert abs(rep.f_true_last - tr.ftrue[-1]) <= 1e-3 * tr.ftrue[-1]
 
 
 def test_solver_outputs_feasible_and_match_report():

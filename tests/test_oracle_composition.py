@@ -127,3 +127,32 @@ def test_block_update_pairs_with_extrapolated_blocks():
         # after the decision A_hat_k and A_k coincide (Alg. 2 sets one to the other)
         prev_hat = tr.A_after(k)
     assert moved > 1e-3     # extrapolated and updated blocks differ: pairing on A would fail
+
+
+def test_forced_decisions_follow_alg2_branches():
+    # the tests' tie-following hook: forcing the decision the comparison would take changes
+    # nothing; forcing the other one takes that branch of Alg. 2 with its beta updates
+    # (eqs. HER_eq:beta_update, HER_eq:beta_bar_update) and keeps F-hat_{k-1} <- F-hat_k
+    T, init = _problem()
+    K = 20
+    _, a = oracle.solve(T, init, K, her=True, track_factors=True)
+    _, same = oracle.solve(T, init, K, her=True, force=a.restart.astype(np.int32))
+    np.testing.assert_array_equal(same.fhat, a.fhat)
+    k = 4
+    force = np.full(K, -1, dtype=np.int32)
+    force[k] = 1 - a.restart[k]
+    _, b = oracle.solve(T, init, K, her=True, force=force, track_factors=True)
+    np.testing.assert_array_equal(b.fhat[:k + 1], a.fhat[:k + 1])
+    assert b.restart[k] == 1 - a.restart[k]
+    beta_prev, bar_prev = a.beta[k - 1], a.beta_bar[k - 1]
+    if b.restart[k]:
+        assert b.beta[k] == pytest.approx(beta_prev / 1.5) and b.beta_bar[k] == pytest.approx(beta_prev)
+        src = b.A_updated(k + 1)
+    else:
+        assert b.beta[k] == pytest.approx(min(bar_prev, 1.05 * beta_prev))
+        assert b.beta_bar[k] == pytest.approx(min(1.0, 1.01 * bar_prev))
+        src = b.A_hat(k + 1)
+    for x, y in zip(b.A_after(k + 1), src):
+        np.testing.assert_array_equal(x, y)
+    # the next decision compares against this iteration's real F-hat
+    assert b.restart[k + 1] == int(b.fhat[k + 1] > b.fhat[k])
