@@ -509,7 +509,9 @@ def wl_streamed(ntf, torch, dev, stream, peaks, T, init):
     with torch.cuda.stream(stream):
         for n in range(3):
             ntf.mttkrp_streamed(Th, init_d, n)
-    mt = [_timed(torch, stream, lambda n=n: ntf.mttkrp_streamed(Th, init_d, n), 3) for n in range(3)]
+    # median of 5 single calls per mode: the host link's rate varies from call to call
+    mt = [statistics.median(_timed(torch, stream, lambda n=n: ntf.mttkrp_streamed(Th, init_d, n), 1)
+                            for _ in range(5)) for n in range(3)]
     mean_ms = sum(mt) / 3
     ach = T.nbytes / (mean_ms * 1e-3) / 1e9
     out = {"dims": list(T.shape), "dtype": "f32", "slab_rows": "default (64 MB slabs)",

@@ -126,6 +126,18 @@ static int tf32_mode() {
     return m;
 }
 
+// Target of scheduled tiles per CTA below which the tensor-core row streams split row tiles into
+// column segments (NTF_SEG_TILES, read once per process; 2 by default).
+static int seg_tiles_per_cta() {
+    static int v = 0;
+    if (!v) {
+        const char* e = std::getenv("NTF_SEG_TILES");
+        const int x = e ? std::atoi(e) : 0;
+        v = x >= 1 && x <= 64 ? x : 2;
+    }
+    return v;
+}
+
 ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     if (rank < 1 || rank > NTF_MAX_RANK) return fail(NTF_EINVAL, "rank must be in [1, 64]");
     if (mode < 0 || mode >= v.order) return fail(NTF_EINVAL, "mode out of range");
@@ -174,10 +186,11 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
     } else {
         const int per_sm = (P.tc && !P.tf32 && 2 * tc_rows_smem(P.RPH) <= 227 * 1024) ? 2 : 1;
         const int64_t cap = (int64_t)sms * per_sm;
-        if (P.tile_slots && P.n_tiles < 2 * cap && P.n_kc >= 8) {
+        const int per_cta = seg_tiles_per_cta();
+        if (P.tile_slots && P.n_tiles < per_cta * cap && P.n_kc >= 8) {
             // Few row tiles with long rows (e.g. merged modes): split each row tile into column
-            // segments of at least 4 chunks so that every CTA gets about two tiles to stream
-            const int64_t want = ceil_div(2 * cap, P.n_tiles);
+            // segments of at least 4 chunks so that every CTA gets about per_cta tiles to stream
+            const int64_t want = ceil_div(per_cta * cap, P.n_tiles);
             const int64_t most = P.n_kc / 4;
             const int64_t ncs = std::max<int64_t>(1, std::min(want, most));
             P.kc_per = (int)ceil_div(P.n_kc, ncs);
