@@ -46,12 +46,6 @@ __device__ __forceinline__ int64_t packed_index_tf32(int64_t i, int nn, int rph)
     return ((kc * N + nn) * 128 + (((kl >> 2) ^ (nn & 7)) << 4) + (kl & 3) * 4) / 4;
 }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    return __uint_as_float(h);
-}
-
 // write row `row`, column `lane` of the next stream's operand (bf16 hi | lo or TF32 hi | lo)
 __device__ __forceinline__ void pack_store(__nv_bfloat16* dst, int64_t row, int lane, int rph, int tf32, float x) {
     if (tf32) {
@@ -193,13 +187,9 @@ __global__ void k_prep(const PrepParams P) {
                 const int64_t i = kc * 32 + kl;
                 const int p = nn < P.RPH ? nn : nn - P.RPH;
                 const float x = (i < P.fct_rows && p < P.r) ? src[i * P.r + p] : 0.f;
-                uint32_t h;
-                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-                const float hi = __uint_as_float(h);
-                uint32_t l;
-                asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+                const float hi = tf32_rna(x);
                 reinterpret_cast<float*>(P.FcT)[((kc * N + nn) * 128 + (((kl >> 2) ^ (nn & 7)) << 4) + (kl & 3) * 4) / 4] =
-                    nn < P.RPH ? hi : __uint_as_float(l);
+                    nn < P.RPH ? hi : tf32_rna(x - hi);
             } else {
                 // tensor-core B operand: bf16 hi | lo columns, 128-byte rows, swizzled like a TMA box
                 const float* src = src_fc;

@@ -297,13 +297,9 @@ __global__ void k_pack_fct_tf32(const float* __restrict__ A, int64_t rows, int r
         const int64_t k = kc * 32 + kl;
         const int p = n < RPH ? n : n - RPH;
         const float x = (k < rows && p < r) ? A[k * r + p] : 0.f;
-        uint32_t h;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-        const float hi = __uint_as_float(h);
-        uint32_t l;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+        const float hi = tf32_rna(x);
         const int64_t byte = (kc * N + n) * 128 + (((kl >> 2) ^ (n & 7)) << 4) + (kl & 3) * 4;
-        out[byte / 4] = n < RPH ? hi : __uint_as_float(l);
+        out[byte / 4] = n < RPH ? hi : tf32_rna(x - hi);
     }
 }
 
@@ -331,13 +327,9 @@ __global__ void k_pack_kr(KrPack K) {
             x = Aa[ka * K.r + p] * Ab[kb * K.r + p];
         }
         if (K.tf32) {
-            uint32_t h;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-            const float hi = __uint_as_float(h);
-            uint32_t l;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
+            const float hi = tf32_rna(x);
             const int64_t byte = (kc * N + n) * 128 + (((kl >> 2) ^ (n & 7)) << 4) + (kl & 3) * 4;
-            static_cast<float*>(K.out)[byte / 4] = n < K.RPH ? hi : __uint_as_float(l);
+            static_cast<float*>(K.out)[byte / 4] = n < K.RPH ? hi : tf32_rna(x - hi);
         } else {
             const __nv_bfloat16 hi = __float2bfloat16_rn(x);
             const __nv_bfloat16 v = n < K.RPH ? hi : __float2bfloat16_rn(x - __bfloat162float(hi));

@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                     }
                 }
             }
+            fence_proxy_async_smem();
             __syncwarp();
             if (ok && lane == 0) mbar_arrive(&empty[stage]);
             if (++stage == kStreamStages) { stage = 0; phase ^= 1u; }
@@ -500,6 +501,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1)
                 }
             }
         }
+        fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[stage]);
         if (++stage == kStreamStages) { stage = 0; phase ^= 1u; }

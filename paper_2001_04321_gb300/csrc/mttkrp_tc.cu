@@ -673,12 +673,6 @@ constexpr int kTfBars = 512;           // barrier block (50 barriers, TMEM slot,
 constexpr uint32_t kTfAcol = kTfAccCols * kTfDbuf;
 constexpr uint32_t kTfCols = 512;
 
-__device__ __forceinline__ float tf32_round(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
 // Instruction descriptor, kind::tf32: FP32 accumulate, A and B TF32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -725,11 +719,92 @@ __device__ __forceinline__ void drain_ring(uint64_t* full, int R, int64_t issued
         }
 }
 
+// The rows kernel tells the three consumers of a chunk's operands and result with one commit
+// per chunk (done[g % 8]): the epilogue (accumulator ready), the converter group of chunk g + 4
+// (A slot free) and the factor-chunk producer of chunk g + 8 (factor slot free).  Each waits
+// on the phase of its own chunk before that barrier can complete the next one: chunk g + 8
+// needs the accumulator of chunk g + 4 released (the epilogue reads in order), its A slot
+// written by the converters after chunk g + 4, and its factor chunk loaded, so no waiter sees
+// a phase twice removed.
+constexpr int kTrThreads = 512;
+constexpr int kTrMmaWarps = 2;
+constexpr int kTrDone = 8;             // done barriers: lcm of the accumulator / A (4) and factor (8) rings
+constexpr int kTrBWarp = 15;           // factor-chunk producer
+
+// D (+)= A x B (A in tensor memory) by the lane whose predicate `leader` is set (elected once
+// per warp, so every MMA and the commit that tracks it come from the same thread)
+__device__ __forceinline__ void tc_mma_tf32_ts_lead(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                                    uint32_t idesc, uint32_t accumulate, uint32_t leader) {
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "setp.ne.b32 e, %5, 0;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate), "r"(leader)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit_lead(uint64_t* bar, uint32_t leader) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "setp.ne.b32 e, %1, 0;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(smem_u32(bar)),
+        "r"(leader)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t elect_leader() {
+    uint32_t e;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(e));
+    return e;
+}
+
+// 32 lanes x 32 bit, 8 consecutive columns per thread
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// y[p] += D[col0 + p] + D[col0 + RPH + p]: the hi and lo halves of one accumulator, read 16 (or
+// 8) columns of each at a time so that no more than 32 loaded values are live
+template <int RPH>
+__device__ __forceinline__ void add_rows(uint32_t tmem_row, int col0, float (&y)[RPH]) {
+#pragma unroll
+    for (int c = 0; c < RPH; c += 16) {
+        if (RPH - c >= 16) {
+            float h[16], l[16];
+            tmem_ld16(tmem_row + col0 + c, h);
+            tmem_ld16(tmem_row + col0 + RPH + c, l);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) y[c + i] += h[i] + l[i];
+        } else {
+            float h[8], l[8];
+            tmem_ld8(tmem_row + col0 + c, h);
+            tmem_ld8(tmem_row + col0 + RPH + c, l);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) y[c + i] += h[i] + l[i];
+        }
+    }
+}
+
 template <int RPH, bool INNER>
-__global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
+__global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
     constexpr int N = 2 * RPH;
     constexpr int kB = N * 128;                       // factor chunk: N rows x 32 fp32 (swizzled)
     constexpr uint32_t kIdesc = idesc_tf32(128, N);
+    static_assert(kTfDbuf == 4 && kTfA == 4 && kTrMmaWarps == 2 && kTrDone % kTfB == 0 && kTrDone % kTfA == 0,
+                  "chunk g owns accumulator and A slot g % 4; chunk pairs alternate between two MMA warps");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -740,13 +815,11 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
     uint64_t* rfull = reinterpret_cast<uint64_t*>(misc);           // box landed
     uint64_t* rempty = rfull + kTfRaw;                             // box read by the 4 converter warps
     uint64_t* bfull = rempty + kTfRaw;                             // factor chunk landed
-    uint64_t* bempty = bfull + kTfB;                               // factor chunk used by the MMAs
-    uint64_t* afull = bempty + kTfB;                               // A slot written by the 4 converter warps
-    uint64_t* aempty = afull + kTfA;                               // A slot used by the MMAs
-    uint64_t* tfull = aempty + kTfA;                               // [kTfDbuf] accumulators ready
-    uint64_t* tempty = tfull + kTfDbuf;                            // [kTfDbuf] accumulators read
-    uint64_t* drain = tempty + kTfDbuf;                            // [2]: one per MMA warp
-    uint64_t* sfull = drain + 2;                                   // [kTileRing]
+    uint64_t* afull = bfull + kTfB;                                // A slot written by the 4 converter warps
+    uint64_t* done = afull + kTfA;                                 // [kTrDone] chunk's MMAs complete
+    uint64_t* tempty = done + kTrDone;                             // [kTfDbuf] accumulator read
+    uint64_t* drain = tempty + kTfDbuf;                            // [kTrMmaWarps]
+    uint64_t* sfull = drain + kTrMmaWarps;                         // [kTileRing]
     uint64_t* sempty = sfull + kTileRing;                          // [kTileRing]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + kTileRing);
     int* tile_ring = reinterpret_cast<int*>(tmem_slot + 1);
@@ -759,23 +832,15 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
             mbar_init(&rfull[s], 1);
             mbar_init(&rempty[s], 4);
         }
-        for (int s = 0; s < kTfB; ++s) {
-            mbar_init(&bfull[s], 1);
-            mbar_init(&bempty[s], 1);
-        }
-        for (int s = 0; s < kTfA; ++s) {
-            mbar_init(&afull[s], 4);
-            mbar_init(&aempty[s], 1);
-        }
-        for (int b = 0; b < kTfDbuf; ++b) {
-            mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
-        }
-        mbar_init(&drain[0], 1);
-        mbar_init(&drain[1], 1);
+        for (int s = 0; s < kTfB; ++s) mbar_init(&bfull[s], 1);
+        for (int s = 0; s < kTfA; ++s) mbar_init(&afull[s], 4);
+        for (int s = 0; s < kTrDone; ++s) mbar_init(&done[s], 1);
+        for (int b = 0; b < kTfDbuf; ++b) mbar_init(&tempty[b], 4);
+        for (int w = 0; w < kTrMmaWarps; ++w) mbar_init(&drain[w], 1);
         for (int k = 0; k < kTileRing; ++k) {
             mbar_init(&sfull[k], 1);
-            mbar_init(&sempty[k], 7 + 4 * kTfConvGroups);   // 2 MMA, 4 epilogue, B producer, converters
+            // 4 MMA warps, 4 epilogue warps, the factor producer, the converters
+            mbar_init(&sempty[k], kTrMmaWarps + 5 + 4 * kTfConvGroups);
         }
         fence_mbar_init();
     }
@@ -805,7 +870,7 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
     pdl_wait();
     pdl_trigger();
 
-    if (warp == kTfBWarp) {
+    if (warp == kTrBWarp) {
         // --------------------- factor-chunk producer (all tiles alike) ---------------------
         if (lane == 0) {
             const unsigned char* FcT = P.cur ? P.FcTb[__ldcg(P.cur + P.fct_sel)] : P.FcT;
@@ -825,7 +890,9 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
                 tile_chunks(P, t, tb, kc0, kc1);
                 for (int kc = kc0; kc < kc1; ++kc, ++g) {
                     const int bs = (int)(g % kTfB);
-                    if (!mbar_wait_bounded(&bempty[bs], (uint32_t)((g / kTfB) & 1) ^ 1u)) {
+                    // slot bs last held chunk g - kTfB: wait for that chunk's MMAs
+                    if (g >= kTfB && !mbar_wait_bounded(&done[(g - kTfB) % kTrDone],
+                                                        (uint32_t)(((g - kTfB) / kTrDone) & 1))) {
                         record_device_error(P.err, kErrWaitEmpty);
                         ok = false;
                         break;
@@ -884,7 +951,7 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
         return;
     }
 
-    if (warp >= 6 && warp < kTfMmaWarp2) {
+    if (warp >= 6 && warp < 6 + 4 * kTfConvGroups) {
         // ------------------------------ converters ------------------------------
         // warp w may reach TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31: tile row m = TMEM lane m.
         // Group cg converts the chunks g with g % kTfConvGroups == cg, so that the latency of
@@ -928,17 +995,19 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
                     v[4 * j + 2] = x.z;
                     v[4 * j + 3] = x.w;
                 }
+                fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&rempty[rs]);
                 uint32_t hi[32], lo[32];
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    const float h = tf32_round(v[i]);
+                    const float h = tf32_rna(v[i]);
                     hi[i] = __float_as_uint(h);
-                    lo[i] = __float_as_uint(tf32_round(v[i] - h));
+                    lo[i] = __float_as_uint(tf32_rna(v[i] - h));
                 }
+                // A slot g % 4 last held chunk g - 4: wait for that chunk's MMAs
                 const int a = (int)(g % kTfA);
-                if (!warp_wait(&aempty[a], (uint32_t)((g / kTfA) & 1) ^ 1u)) {
+                if (g >= kTfA && !warp_wait(&done[(g - kTfA) % kTrDone], (uint32_t)(((g - kTfA) / kTrDone) & 1))) {
                     if (lane == 0) record_device_error(P.err, kErrWaitEmpty);
                     ok = false;
                     break;
@@ -957,13 +1026,43 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
 
     if (warp == 5 || warp == kTfMmaWarp2) {
         // ------------------------------ MMA issuers ------------------------------
-        // Each warp runs the loop as a whole, and one elected lane issues the MMAs and
-        // commits.  A single issuing warp was measured at about 105 cycles per MMA whatever
-        // the shape, so two warps take the chunks in turn (mg = chunk parity): the
-        // accumulators, A slot and factor slot of a chunk all have the chunk's parity.
+        // The 8 MMAs of one chunk accumulate into one tensor-memory accumulator, so each waits
+        // for the one before it (about 90 cycles), and the tensor pipe runs them in issue
+        // order.  A warp therefore takes two chunks at a time (g, g + 1) and interleaves their
+        // MMAs, so that two independent chains share the pipe.  Warp 5 takes the pairs with
+        // g % 4 == 0, warp 14 those with g % 4 == 2; chunk g keeps accumulator and A slot g % 4.
+        // A first chunk waits for its partner, which may come with the next tile; the CTA's
+        // last chunk may have none and goes alone.  The issuing lane is elected once, and it
+        // also commits.
         const int mg = warp == 5 ? 0 : 1;
+        const uint32_t leader = elect_leader();
         int64_t g = 0;
-        bool ok = true;
+        bool ok = true, pending = false;
+        auto issue = [&](int64_t c0, int n) -> bool {
+            for (int j = 0; j < n; ++j) {
+                const int64_t c = c0 + j;
+                if (!warp_wait(&tempty[c % kTfDbuf], (uint32_t)((c / kTfDbuf) & 1) ^ 1u) ||
+                    !warp_wait(&afull[c % kTfA], (uint32_t)((c / kTfA) & 1)) ||
+                    !warp_wait(&bfull[c % kTfB], (uint32_t)((c / kTfB) & 1))) {
+                    if (lane == 0) record_device_error(P.err, kErrWaitFull);
+                    return false;
+                }
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {       // T_lo x [F_hi | F_lo] first (kk < 4), then T_hi on top
+                for (int j = 0; j < n; ++j) {
+                    const int64_t c = c0 + j;
+                    const uint32_t b0 = base + (uint32_t)(kTfRaw * kTfBox + (int)(c % kTfB) * kB);
+                    const uint32_t dt = tmem + (uint32_t)((int)(c % kTfDbuf) * kTfAccCols);
+                    const uint32_t at = tmem + kTfAcol + (uint32_t)((int)(c % kTfA) * 64) + (kk < 4 ? 32u : 0u);
+                    tc_mma_tf32_ts_lead(dt, at + (kk & 3) * 8, smem_desc_sw128(b0 + (kk & 3) * 32, 16, 1024), kIdesc,
+                                        kk > 0 ? 1u : 0u, leader);
+                }
+            }
+            for (int j = 0; j < n; ++j) tc_commit_lead(&done[(c0 + j) % kTrDone], leader);
+            return true;
+        };
         for (int64_t s = 0; ok; ++s) {
             const int slot = (int)(s % kTileRing);
             if (!warp_wait(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
@@ -977,36 +1076,21 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
             int64_t tb;
             int kc0, kc1;
             tile_chunks(P, t, tb, kc0, kc1);
-            for (int kc = kc0; kc < kc1; ++kc, ++g) {
-                if ((int)(g & 1) != mg) continue;
-                const int d = (int)(g % kTfDbuf), a = (int)(g % kTfA), bs = (int)(g % kTfB);
-                if (!warp_wait(&tempty[d], (uint32_t)((g / kTfDbuf) & 1) ^ 1u) ||
-                    !warp_wait(&afull[a], (uint32_t)((g / kTfA) & 1)) ||
-                    !warp_wait(&bfull[bs], (uint32_t)((g / kTfB) & 1))) {
-                    if (lane == 0) record_device_error(P.err, kErrWaitFull);
-                    ok = false;
-                    break;
+            for (int kc = kc0; kc < kc1 && ok; ++kc, ++g) {
+                if ((int)((g >> 1) & 1) != mg) continue;
+                if ((g & 1) == 0) {
+                    pending = true;
+                } else {
+                    ok = issue(g - 1, 2);
+                    pending = false;
                 }
-                tc_fence_after();
-                const uint32_t b0 = base + (uint32_t)(kTfRaw * kTfBox + bs * kB);
-                const uint32_t dt = tmem + (uint32_t)(d * kTfAccCols);
-                const uint32_t at = tmem + kTfAcol + (uint32_t)(a * 64);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk)     // T_lo x [F_hi | F_lo], first accumulator
-                    tc_mma_tf32_ts_elect(dt, at + 32 + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc,
-                                         kk > 0 ? 1u : 0u);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk)     // T_hi x [F_hi | F_lo] on top
-                    tc_mma_tf32_ts_elect(dt, at + kk * 8, smem_desc_sw128(b0 + kk * 32, 16, 1024), kIdesc, 1u);
-                tc_commit_elect(&aempty[a]);
-                tc_commit_elect(&bempty[bs]);
-                tc_commit_elect(&tfull[d]);
             }
         }
-        tc_commit_elect(&drain[mg]);
+        if (ok && pending) ok = issue(g - 1, 1);
+        tc_commit_lead(&drain[mg], leader);
         if (!warp_wait(&drain[mg], 0) && lane == 0) record_device_error(P.err, kErrWaitDrain);
         __syncwarp();
-        named_bar_sync(2, 192);
+        named_bar_sync(2, 128 + 32 * kTrMmaWarps);
         if (warp == 5) {
             tc_fence_after();
             tmem_dealloc(tmem, kTfCols);
@@ -1037,39 +1121,35 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
         int kc0, kc1;
         tile_chunks(P, t, tb, kc0, kc1);
         tile_coords<INNER>(P, tb, ib, ot);
-        float w[RPH];
         bool row_live;
+        const float* wsrc;
         if (INNER) {
             const int64_t o = ot * P.O_T + m / P.I_T;
             row_live = o < P.n_o && ib * P.I_T + m % P.I_T < P.Ii;
-            const float* src = Wt + (row_live ? o : 0) * P.ldw;
-#pragma unroll
-            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(src + p) : 0.f;
+            wsrc = Wt + (row_live ? o : 0) * P.ldw;
         } else {
             const int64_t i = ib * 128 + m;
             row_live = i < P.Ii;
-            const float* src = Fit + (row_live ? i : 0) * P.ldw;
-#pragma unroll
-            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(src + p) : 0.f;
+            wsrc = Fit + (row_live ? i : 0) * P.ldw;
         }
+        float w[RPH];
+#pragma unroll
+        for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(wsrc + p) : 0.f;
         float y[RPH];
 #pragma unroll
         for (int p = 0; p < RPH; ++p) y[p] = 0.f;
         for (int kc = kc0; kc < kc1; ++kc, ++gq) {
             const int d = (int)(gq % kTfDbuf);
-            if (ok && !warp_wait(&tfull[d], (uint32_t)((gq / kTfDbuf) & 1))) {
+            if (ok && !warp_wait(&done[gq % kTrDone], (uint32_t)((gq / kTrDone) & 1))) {
                 if (lane == 0) record_device_error(P.err, kErrWaitFull);
                 ok = false;
             }
             if (ok) {
                 tc_fence_after();
-                float yc[RPH];
-                read_rows<RPH>(tmem_row, d * kTfAccCols, yc);
+                add_rows<RPH>(tmem_row, d * kTfAccCols, y);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[d]);
-#pragma unroll
-                for (int p = 0; p < RPH; ++p) y[p] += yc[p];
             }
         }
         if (INNER) {
@@ -1116,7 +1196,7 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_rows(const __grid_consta
         }
     }
     tc_fence_before();
-    named_bar_sync(2, 192);
+    named_bar_sync(2, 128 + 32 * kTrMmaWarps);
 }
 
 // ----------------------------------------------------------------------------
@@ -1268,14 +1348,15 @@ __global__ void __launch_bounds__(kTfThreads, 1) k_tf32_last(const __grid_consta
 #pragma unroll
             for (int i = 0; i < 32; ++i)
                 v[i] = *reinterpret_cast<const float*>(box + i * 128 + (((lane >> 2) ^ (i & 7)) << 4));
+            fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&rempty[rs]);
             uint32_t hi[32], lo[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
-                const float h = tf32_round(v[i]);
+                const float h = tf32_rna(v[i]);
                 hi[i] = __float_as_uint(h);
-                lo[i] = __float_as_uint(tf32_round(v[i] - h));
+                lo[i] = __float_as_uint(tf32_rna(v[i] - h));
             }
             const int a = (int)(k % kTfA);
             if (!warp_wait(&aempty[a], (uint32_t)((k / kTfA) & 1) ^ 1u)) {
@@ -1384,7 +1465,7 @@ cudaError_t launch_tf32_impl(int kind, dim3 grid, size_t smem, cudaStream_t st, 
         set_bytes[kind] = smem;
     }
     if (grid.x == 0) return cudaSuccess;
-    return launch_kernel(k, grid, dim3(kTfThreads), smem, st, pdl, map, P);
+    return launch_kernel(k, grid, dim3(kind == 2 ? kTfThreads : kTrThreads), smem, st, pdl, map, P);
 }
 
 template <int RPH>

@@ -145,3 +145,22 @@ def test_fp32_kernel_selection(mode):
     env = dict(os.environ, NTF_TF32=mode)
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0 and "ok" in out.stdout, out.stderr[-2000:]
+
+
+@pytest.mark.parametrize("dims,r", [((300, 300, 300), 32), ((200, 330, 250), 20)])
+def test_fp32_tensor_core_streams_repeat_exactly(dims, r):
+    # The 3xTF32 row streams hand chunks to four MMA warps and take tiles from a run-time
+    # counter; every tile writes its own slot, so repeated launches must agree bit for bit,
+    # and each must match the oracle.  Ten chunks per row tile in mode 0 (300 columns).
+    import torch
+    import paper_2001_04321_gb300 as ntf
+    T, F = _problem(dims, r, 11)
+    buf, d, ld = device_tensor(T, "f32")
+    Fd = [torch.from_numpy(A).cuda() for A in F]
+    for n in range(len(dims)):
+        R = oracle.mttkrp(T, F, n)
+        first = ntf.mttkrp(buf, Fd, n, dims=d, ld=ld).cpu().numpy()
+        assert rel_fro(first, R) <= 1e-5, (n, rel_fro(first, R))
+        for _ in range(8):
+            again = ntf.mttkrp(buf, Fd, n, dims=d, ld=ld).cpu().numpy()
+            assert np.array_equal(first, again), (n, float(np.max(np.abs(first - again))))
