@@ -184,7 +184,8 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
         if (gs > P.n_tiles) gs = (int)P.n_tiles;
         P.G = gs;
     } else {
-        const int per_sm = (P.tc && !P.tf32 && 2 * tc_rows_smem(P.RPH) <= 227 * 1024) ? 2 : 1;
+        const int per_sm =
+            (P.tc && !P.tf32 && tc_rows_ctas_per_sm() >= 2 && 2 * tc_rows_smem(P.RPH) <= 227 * 1024) ? 2 : 1;
         const int64_t cap = (int64_t)sms * per_sm;
         const int per_cta = seg_tiles_per_cta();
         if (P.tile_slots && P.n_tiles < per_cta * cap && P.n_kc >= 8) {

@@ -33,8 +33,14 @@ namespace ntf {
 namespace {
 
 constexpr int kTcThreads = 192;
-constexpr int kTcStages = 4;
+constexpr int kTcStages = 4;        // last-mode kernel: stages of two boxes
+constexpr int kRowStages = 4;       // rows kernel: stages of one box and one factor chunk
 constexpr int kDbuf = 4;             // rows kernel: TMEM accumulators in flight (64 columns each)
+constexpr int kRowCtasPerSm = kRowStages * kDbuf <= 16 ? 2 : 1;
+// rows kernel: barriers (full, empty per stage; tfull, tempty per accumulator; drain; sfull,
+// sempty per tile-ring slot) and the TMEM slot, then the tile ring of 4 records (80 bytes)
+constexpr int kRowBarBytes = ((2 * kRowStages + 2 * kDbuf + 1 + 2 * 4) * 8 + 8 + 15) / 16 * 16;
+constexpr int kRowMiscBytes = (kRowBarBytes + 128 + 255) / 256 * 256;
 constexpr int kBoxBytes = 16384;   // 128 rows x 64 bf16
 
 // ----------------------------------------------------------------------------
@@ -138,33 +144,196 @@ __device__ __forceinline__ void read_rows(uint32_t tmem_row, int col0, float (&y
 // tiles (no tail of slow CTAs).
 // ----------------------------------------------------------------------------
 constexpr int kTileRing = 4;
-
-// inner mode: tiles run over the inner blocks first; outer modes over the outer index first
-template <bool INNER>
-__device__ __forceinline__ void tile_coords(const TcParams& P, int64_t t, int64_t& ib, int64_t& ot) {
-    if (INNER) { ib = t / P.n_ot; ot = t % P.n_ot; }
-    else { ot = t / P.nb; ib = t % P.nb; }
-}
-
-// A scheduled tile t is row tile t / n_cs restricted to its column segment t % n_cs: the
-// chunks [kc0, kc1).  With one segment (the usual case) it is the whole row tile.  Every
-// scheduled tile has its own output slot, so the segments' partial sums meet only in the
-// fixed-order reduction.
-__device__ __forceinline__ void tile_chunks(const TcParams& P, int64_t t, int64_t& tb, int& kc0, int& kc1) {
-    const int ncs = P.n_cs > 0 ? P.n_cs : 1;
-    const int per = P.kc_per > 0 ? P.kc_per : P.n_kc;
-    tb = t / ncs;
-    kc0 = (int)(t - tb * ncs) * per;
-    kc1 = kc0 + per < P.n_kc ? kc0 + per : P.n_kc;
-}
+static_assert(kTileRing == 4, "the rows kernels' barrier blocks hold 4 tile-ring slots");
 
 // the statically assigned first tile of this CTA (-1 if there is none)
 __device__ __forceinline__ int g_first_tile(int64_t n_tiles) {
     return (int64_t)blockIdx.x < n_tiles ? (int)blockIdx.x : -1;
 }
 
+// wait until the last min(issued, R) loads of a ring of R stages have landed
+__device__ __forceinline__ void drain_ring(uint64_t* full, int R, int64_t issued, int* err) {
+    const int64_t lo = issued > R ? issued - R : 0;
+    for (int64_t i = issued - 1; i >= lo; --i)
+        if (!mbar_wait_bounded(&full[i % R], (uint32_t)((i / R) & 1))) {
+            record_device_error(err, kErrWaitDrain);
+            break;
+        }
+}
+
+// A scheduled tile as the producer decodes it, once, for every consumer warp: its slot t,
+// its chunks [kc0, kc1), and its row block ib and outer block ot.  (Each warp role decoding
+// the index itself with 64-bit divisions took thousands of cycles at every tile boundary, on
+// the epilogue's critical path.)  Tile counts are below 2^31, so 32-bit arithmetic holds.
+// Scheduled tile t is row tile tb = t / n_cs restricted to its column segment t % n_cs; with
+// one segment (the usual case) that is the whole row tile.  Every scheduled tile has its own
+// output slot, so the segments' partial sums meet only in the fixed-order reduction.  The
+// inner mode numbers row tiles over the outer blocks first (tb = ib n_ot + ot), the outer
+// modes over the row blocks first (tb = ot nb + ib).
+struct TileRec {
+    int t, kc0, kc1, ib, ot;
+};
+
+template <bool INNER>
+__device__ __forceinline__ TileRec decode_tile(const TcParams& P, int t) {
+    TileRec r{t, 0, 0, 0, 0};
+    if (t < 0) return r;
+    const unsigned int ncs = P.n_cs > 0 ? (unsigned int)P.n_cs : 1u;
+    const int per = P.kc_per > 0 ? P.kc_per : P.n_kc;
+    const unsigned int tb = (unsigned int)t / ncs;
+    r.kc0 = (int)((unsigned int)t - tb * ncs) * per;
+    r.kc1 = r.kc0 + per < P.n_kc ? r.kc0 + per : P.n_kc;
+    if (INNER) {
+        const unsigned int n_ot = (unsigned int)P.n_ot;
+        r.ib = (int)(tb / n_ot);
+        r.ot = (int)(tb - (unsigned int)r.ib * n_ot);
+    } else {
+        const unsigned int nb = (unsigned int)P.nb;
+        r.ot = (int)(tb / nb);
+        r.ib = (int)(tb - (unsigned int)r.ot * nb);
+    }
+    return r;
+}
+
+// values a lane holds before xor step LVL (offsets 16, 8, 4, 2, 1) of halving_sum
+__host__ __device__ constexpr int halving_count(int n, int lvl) {
+    return lvl == 0 ? n : (halving_count(n, lvl - 1) % 2 == 0 ? halving_count(n, lvl - 1) / 2 : halving_count(n, lvl - 1));
+}
+
+// Sum of z[0..N) over the 32 lanes by recursive halving: at each xor step a lane keeps the
+// half of its values that its lane bit selects and adds the partner's copy of that half, so
+// each step exchanges half as many values as the one before (27 shuffles for N = 24, against
+// 120 for a butterfly on every value).  Once the held values no longer split evenly the
+// remaining steps add all of them.  Afterwards lane L holds, in z[0..halving_count(N, 5)),
+// the sums of values halving_base<N>(L) + j.  Every sum has a fixed order.
+template <int N, int LVL>
+struct HalvingStep {
+    static __device__ __forceinline__ void run(float (&z)[N], int lane) {
+        constexpr int n = halving_count(N, LVL);
+        constexpr int off = 16 >> LVL;
+        if constexpr (n % 2 == 0) {
+            constexpr int h = n / 2;
+            const bool up = (lane & off) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+                const float send = up ? z[i] : z[h + i];
+                const float keep = up ? z[h + i] : z[i];
+                z[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < n; ++i) z[i] += __shfl_xor_sync(0xffffffffu, z[i], off);
+        }
+        HalvingStep<N, LVL + 1>::run(z, lane);
+    }
+};
+template <int N>
+struct HalvingStep<N, 5> {
+    static __device__ __forceinline__ void run(float (&)[N], int) {}
+};
+
+// first value index held by lane L after HalvingStep<N, 0>::run
+template <int N>
+__device__ __forceinline__ int halving_base(int lane) {
+    int b = 0;
+#pragma unroll
+    for (int lvl = 0; lvl < 5; ++lvl) {
+        const int n = halving_count(N, lvl);
+        if (n % 2 == 0 && (lane & (16 >> lvl))) b += n / 2;
+    }
+    return b;
+}
+// lane bits whose lanes hold copies of the same sums (the steps that added all values)
+template <int N>
+__host__ __device__ constexpr int halving_dup_mask() {
+    int m = 0;
+    for (int lvl = 0; lvl < 5; ++lvl)
+        if (halving_count(N, lvl) % 2 != 0) m |= 16 >> lvl;
+    return m;
+}
+
+// The epilogue warps' row weights for one tile (w[p] = 0 for dead rows and p >= r): inner mode
+// W(o, :) of the row's outer index, outer modes the row's own weight row.
 template <int RPH, bool INNER>
-__global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
+__device__ __forceinline__ void tile_weights(const TcParams& P, const TileRec& tr, int m, int m_o, int m_i,
+                                             const float* Wt, const float* Fit, float (&w)[RPH]) {
+    bool row_live;
+    const float* src;
+    if (INNER) {
+        const int64_t o = (int64_t)tr.ot * P.O_T + m_o;
+        row_live = o < P.n_o && (int64_t)tr.ib * P.I_T + m_i < P.Ii;
+        src = Wt + (row_live ? o : 0) * P.ldw;
+    } else {
+        const int64_t i = (int64_t)tr.ib * 128 + m;
+        row_live = i < P.Ii;
+        src = Fit + (row_live ? i : 0) * P.ldw;
+    }
+#pragma unroll
+    for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(src + p) : 0.f;
+}
+
+// A finished tile's output slot from its weighted row sums z (thread m = tile row m), in a
+// fixed order.  The four epilogue warps call this together (it holds named barrier 1).
+//   inner mode: rows m = a I_T + b share inner row b of block ib, so the slot holds their sum
+//     over the tile's O_T outer indices a: lanes with equal lane % I_T by a butterfly, then
+//     the 4 warps through shared memory (red);
+//   outer modes: the sum over all 128 rows: per warp by a butterfly on every value, or by
+//     recursive halving (HALVING; fewer shuffles and adds, measured faster in the TF32 kernel,
+//     where the epilogue shares its issue slots with eight converter warps, and slower in the
+//     bf16 kernel), then the 4 warps through shared memory (zsum, alternate halves per tile so
+//     that one barrier suffices).
+template <int RPH, bool INNER, bool HALVING>
+__device__ __forceinline__ void tile_flush(const TcParams& P, float (&z)[RPH], int t, bool write, int warp, int lane,
+                                           int m, float* red, float* zsum, int& parity) {
+    if (INNER) {
+        for (int off = 16; off >= P.I_T; off >>= 1)
+#pragma unroll
+            for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
+        // (I_T <= 32 divides 32: lane b of every warp now holds that warp's rows of b)
+        if (lane < P.I_T) {
+#pragma unroll
+            for (int p = 0; p < RPH; ++p) red[(warp * 32 + lane) * RPH + p] = z[p];
+        }
+        named_bar_sync(1, 128);
+        if (write) {
+            for (int idx = m; idx < P.I_T * P.r; idx += 128) {
+                const int b = idx / P.r, p = idx - b * P.r;
+                const float sacc = (red[(0 * 32 + b) * RPH + p] + red[(1 * 32 + b) * RPH + p]) +
+                                   (red[(2 * 32 + b) * RPH + p] + red[(3 * 32 + b) * RPH + p]);
+                P.part[((int64_t)t * P.I_T + b) * P.RP + p] = sacc;
+            }
+        }
+        named_bar_sync(1, 128);
+    } else {
+        float* zs = zsum + parity * 128;
+        if (HALVING) {
+            HalvingStep<RPH, 0>::run(z, lane);
+            if ((lane & halving_dup_mask<RPH>()) == 0) {
+                const int b0 = halving_base<RPH>(lane);
+#pragma unroll
+                for (int j = 0; j < halving_count(RPH, 5); ++j) zs[warp * 32 + b0 + j] = z[j];
+            }
+        } else {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
+            float mine = 0.f;
+#pragma unroll
+            for (int p = 0; p < RPH; ++p)
+                if (p == lane) mine = z[p];
+            zs[warp * 32 + lane] = mine;
+        }
+        named_bar_sync(1, 128);
+        if (warp == 0 && lane < P.r && write)
+            P.part[(int64_t)t * P.RP + lane] = (zs[lane] + zs[32 + lane]) + (zs[64 + lane] + zs[96 + lane]);
+        parity ^= 1;
+    }
+}
+
+
+template <int RPH, bool INNER>
+__global__ void __launch_bounds__(kTcThreads, kRowCtasPerSm) k_tc_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
     constexpr int N = 2 * RPH;
     constexpr int kB = N * 128;                 // factor chunk: N rows x 64 bf16 (swizzled)
     constexpr int kStage = kBoxBytes + kB;      // multiple of 1024 (N multiple of 16)
@@ -173,22 +342,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char* base_ptr = smem_raw + (base - raw);
-    uint64_t* full = reinterpret_cast<uint64_t*>(base_ptr + kTcStages * kStage);
-    uint64_t* empty = full + kTcStages;
-    uint64_t* tfull = empty + kTcStages;        // [kDbuf]: accumulator of one 64-column chunk ready
+    uint64_t* full = reinterpret_cast<uint64_t*>(base_ptr + kRowStages * kStage);
+    uint64_t* empty = full + kRowStages;
+    uint64_t* tfull = empty + kRowStages;        // [kDbuf]: accumulator of one 64-column chunk ready
     uint64_t* tempty = tfull + kDbuf;           // [kDbuf]: accumulator read by the epilogue
     uint64_t* drain = tempty + kDbuf;
     uint64_t* sfull = drain + 1;                // [kTileRing]: tile index published
     uint64_t* sempty = sfull + kTileRing;       // [kTileRing]: tile index read by all consumers
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + kTileRing);
-    int* tile_ring = reinterpret_cast<int*>(tmem_slot + 1);                          // [kTileRing]
-    float* zsum = reinterpret_cast<float*>(base_ptr + kTcStages * kStage + 256);   // [2][4][32]
+    TileRec* tile_ring = reinterpret_cast<TileRec*>(base_ptr + kRowStages * kStage + kRowBarBytes);   // [kTileRing]
+    float* zsum = reinterpret_cast<float*>(base_ptr + kRowStages * kStage + kRowMiscBytes);   // [2][4][32]
     float* red = zsum + 2 * 4 * 32;                                                  // [128][RPH]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < kRowStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -212,20 +381,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
     // be in flight while the kernel before this one finishes (the packed factor chunks,
     // which that kernel writes, follow after the wait)
     const int first_tile = g_first_tile(P.n_tiles);
-    int64_t ftb = 0;
-    int fkc0 = 0, fkc1 = 0;
-    if (first_tile >= 0) tile_chunks(P, first_tile, ftb, fkc0, fkc1);
-    const int npre = first_tile >= 0 ? (fkc1 - fkc0 < kTcStages ? fkc1 - fkc0 : kTcStages) : 0;
+    const TileRec ft = decode_tile<INNER>(P, first_tile);
+    const int npre = first_tile >= 0 ? (ft.kc1 - ft.kc0 < kRowStages ? ft.kc1 - ft.kc0 : kRowStages) : 0;
     if (warp == 4 && lane == 0) {
         prefetch_tensormap(&tmap);
-        if (first_tile >= 0) {
-            int64_t ib, ot;
-            tile_coords<INNER>(P, ftb, ib, ot);
-            for (int j = 0; j < npre; ++j) {
-                mbar_arrive_expect_tx(&full[j], (uint32_t)kStage);
-                tma_load_3d(base_ptr + j * kStage, &tmap, &full[j], (fkc0 + j) * 64, (int)(ib * P.I_T),
-                            (int)(ot * P.O_T));
-            }
+        for (int j = 0; j < npre; ++j) {
+            mbar_arrive_expect_tx(&full[j], (uint32_t)kStage);
+            tma_load_3d(base_ptr + j * kStage, &tmap, &full[j], (ft.kc0 + j) * 64, ft.ib * P.I_T, ft.ot * P.O_T);
         }
     }
     // With P.early the producer and MMA warps do not wait for the kernel before this one and
@@ -254,13 +416,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
                     const unsigned int grab = atomicAdd(P.sched, 1u) + (unsigned int)gridDim.x;
                     t = grab < (unsigned int)P.n_tiles ? (int)grab : -1;
                 }
-                tile_ring[slot] = t;
+                const TileRec tr = s == 0 ? ft : decode_tile<INNER>(P, t);
+                tile_ring[slot] = tr;
                 mbar_arrive(&sfull[slot]);              // releases the slot to the consumers
                 if (t < 0) break;
-                int64_t ib, ot, tb;
-                int kc0, kc1;
-                tile_chunks(P, t, tb, kc0, kc1);
-                tile_coords<INNER>(P, tb, ib, ot);
+                const int kc0 = tr.kc0, kc1 = tr.kc1;
                 bool ok = true;
                 for (int kc = kc0; kc < kc1; ++kc) {
                     unsigned char* st = base_ptr + stage * kStage;
@@ -274,15 +434,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
                             break;
                         }
                         mbar_arrive_expect_tx(&full[stage], (uint32_t)kStage);
-                        tma_load_3d(st, &tmap, &full[stage], kc * 64, (int)(ib * P.I_T), (int)(ot * P.O_T));
+                        tma_load_3d(st, &tmap, &full[stage], kc * 64, tr.ib * P.I_T, tr.ot * P.O_T);
                         bulk_load(st + kBoxBytes, FcT + (int64_t)kc * kB, (uint32_t)kB, &full[stage]);
                     }
                     ++issued;
-                    if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
+                    if (++stage == kRowStages) { stage = 0; phase ^= 1u; }
                 }
                 if (!ok) break;
             }
-            drain_stages(full, stage, phase, issued, P.err);
+            drain_ring(full, kRowStages, issued, P.err);
         }
         return;
     }
@@ -300,14 +460,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
                 if (lane == 0) record_device_error(P.err, kErrWaitFull);
                 break;
             }
-            const int t = tile_ring[slot];
+            const TileRec tr = tile_ring[slot];
             __syncwarp();
             if (lane == 0) mbar_arrive(&sempty[slot]);
-            if (t < 0) break;
-            int64_t tb;
-            int kc0, kc1;
-            tile_chunks(P, t, tb, kc0, kc1);
-            for (int kc = kc0; kc < kc1; ++kc, ++gq) {
+            if (tr.t < 0) break;
+            for (int kc = tr.kc0; kc < tr.kc1; ++kc, ++gq) {
                 const int d = (int)(gq % kDbuf);
                 if (!warp_wait(&tempty[d], (uint32_t)((gq / kDbuf) & 1) ^ 1u) || !warp_wait(&full[stage], phase)) {
                     if (lane == 0) record_device_error(P.err, kErrWaitFull);
@@ -324,7 +481,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
                                  kIdesc, kk > 0 ? 1u : 0u);
                 tc_commit_elect(&empty[stage]);          // frees the stage once these MMAs have read it
                 tc_commit_elect(&tfull[d]);              // this chunk's accumulator is complete
-                if (++stage == kTcStages) { stage = 0; phase ^= 1u; }
+                if (++stage == kRowStages) { stage = 0; phase ^= 1u; }
             }
         }
         // make sure nothing is still running on the tensor cores before TMEM is freed
@@ -344,6 +501,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
     const float* Wt = P.cur ? P.Wb[__ldcg(P.cur + P.w_sel) ^ P.w_flip] : P.W;
     const float* Fit = P.cur ? P.Fib[__ldcg(P.cur + P.fi_sel) ^ P.fi_flip] : P.Fi;
     const int m = threadIdx.x;                       // tile row = TMEM lane
+    const int m_o = m / P.I_T, m_i = m - m_o * P.I_T;   // inner mode: row m = (outer m_o, inner m_i)
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
     int64_t gq = 0;
@@ -354,30 +512,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
             if (lane == 0) record_device_error(P.err, kErrWaitFull);
             break;
         }
-        const int t = tile_ring[slot];
+        const TileRec tr = tile_ring[slot];
         __syncwarp();
         if (lane == 0) mbar_arrive(&sempty[slot]);
-        if (t < 0) break;
-        int64_t ib, ot, tb;
-        int kc0, kc1;
-        tile_chunks(P, t, tb, kc0, kc1);
-        tile_coords<INNER>(P, tb, ib, ot);
-        // weights of this row, fetched while the tile is being contracted
+        if (tr.t < 0) break;
+        const int kc0 = tr.kc0, kc1 = tr.kc1;
+        // this row's weights, fetched while the tile is being contracted
         float w[RPH];
-        bool row_live;
-        if (INNER) {
-            const int64_t o = ot * P.O_T + m / P.I_T;
-            row_live = o < P.n_o && ib * P.I_T + m % P.I_T < P.Ii;
-            const float* src = Wt + (row_live ? o : 0) * P.ldw;
-#pragma unroll
-            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(src + p) : 0.f;
-        } else {
-            const int64_t i = ib * 128 + m;
-            row_live = i < P.Ii;
-            const float* src = Fit + (row_live ? i : 0) * P.ldw;
-#pragma unroll
-            for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(src + p) : 0.f;
-        }
+        tile_weights<RPH, INNER>(P, tr, m, m_o, m_i, Wt, Fit, w);
         // Y(row) = sum over the tile's 64-column chunks of the chunk accumulators (IEEE FP32 adds)
         float y[RPH];
 #pragma unroll
@@ -399,52 +541,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_tc_rows(const __grid_constant
                 for (int p = 0; p < RPH; ++p) y[p] += yc[p];
             }
         }
-        if (INNER) {
-            // rows m = a I_T + b share inner row b of block ib: this tile's slot holds their
-            // weighted sum over the tile's O_T outer indices a.  Lanes with equal lane % I_T
-            // are summed by a butterfly, the 4 warps through shared memory, in a fixed order.
-            float z[RPH];
+        float z[RPH];
 #pragma unroll
-            for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
-            for (int off = 16; off >= P.I_T; off >>= 1)
-#pragma unroll
-                for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
-            // (I_T <= 32 divides 32: lane b of every warp now holds that warp's rows of b)
-            if (lane < P.I_T) {
-#pragma unroll
-                for (int p = 0; p < RPH; ++p) red[(warp * 32 + lane) * RPH + p] = z[p];
-            }
-            named_bar_sync(1, 128);
-            if (ok) {
-                for (int idx = m; idx < P.I_T * P.r; idx += 128) {
-                    const int b = idx / P.r, p = idx - b * P.r;
-                    const float sacc = (red[(0 * 32 + b) * RPH + p] + red[(1 * 32 + b) * RPH + p]) +
-                                       (red[(2 * 32 + b) * RPH + p] + red[(3 * 32 + b) * RPH + p]);
-                    P.part[((int64_t)t * P.I_T + b) * P.RP + p] = sacc;
-                }
-            }
-            named_bar_sync(1, 128);
-        } else {
-            float z[RPH];
-#pragma unroll
-            for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-                for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
-            float mine = 0.f;
-#pragma unroll
-            for (int p = 0; p < RPH; ++p)
-                if (p == lane) mine = z[p];
-            float* zs = zsum + parity * 128;
-            zs[warp * 32 + lane] = mine;
-            named_bar_sync(1, 128);
-            if (warp == 0 && lane < P.r && ok) {
-                const float s4 = (zs[lane] + zs[32 + lane]) + (zs[64 + lane] + zs[96 + lane]);
-                P.part[(int64_t)t * P.RP + lane] = s4;
-            }
-            parity ^= 1;
-        }
+        for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
+        tile_flush<RPH, INNER, false>(P, z, tr.t, ok, warp, lane, m, red, zsum, parity);
     }
     tc_fence_before();
     named_bar_sync(2, 160);
@@ -669,7 +769,7 @@ constexpr int kTfA = 4;                // tensor-memory A slots of 64 columns (T
 constexpr int kTfDbuf = 4;             // chunks whose accumulators are in flight
 constexpr int kTfAccCols = 64;         // one 64-column accumulator per chunk
 constexpr int kTfBox = 16384;          // 128 rows x 32 fp32
-constexpr int kTfBars = 512;           // barrier block (50 barriers, TMEM slot, tile ring)
+constexpr int kTfBars = 512;           // barrier block (50 barriers, TMEM slot, tile ring of 4 records)
 constexpr uint32_t kTfAcol = kTfAccCols * kTfDbuf;
 constexpr uint32_t kTfCols = 512;
 
@@ -707,17 +807,6 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
 }
 
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-
-// wait until the last min(issued, R) loads of a ring of R stages have landed
-__device__ __forceinline__ void drain_ring(uint64_t* full, int R, int64_t issued, int* err) {
-    const int64_t lo = issued > R ? issued - R : 0;
-    for (int64_t i = issued - 1; i >= lo; --i)
-        if (!mbar_wait_bounded(&full[i % R], (uint32_t)((i / R) & 1))) {
-            record_device_error(err, kErrWaitDrain);
-            break;
-        }
-}
 
 // The rows kernel tells the three consumers of a chunk's operands and result with one commit
 // per chunk (done[g % 8]): the epilogue (accumulator ready), the converter group of chunk g + 4
@@ -822,7 +911,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
     uint64_t* sfull = drain + kTrMmaWarps;                         // [kTileRing]
     uint64_t* sempty = sfull + kTileRing;                          // [kTileRing]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + kTileRing);
-    int* tile_ring = reinterpret_cast<int*>(tmem_slot + 1);
+    TileRec* tile_ring = reinterpret_cast<TileRec*>(tmem_slot + 1);   // [kTileRing]
     float* zsum = reinterpret_cast<float*>(misc + kTfBars);        // [2][4][32]
     float* red = zsum + 2 * 4 * 32;                                // [128][RPH]
 
@@ -851,20 +940,13 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
     const uint32_t tmem = *tmem_slot;
     // CTA g's first tile is tile g; its first tensor boxes go out before the wait
     const int first_tile = g_first_tile(P.n_tiles);
-    int64_t ftb = 0;
-    int fkc0 = 0, fkc1 = 0;
-    if (first_tile >= 0) tile_chunks(P, first_tile, ftb, fkc0, fkc1);
-    const int npre = first_tile >= 0 ? (fkc1 - fkc0 < kTfRaw ? fkc1 - fkc0 : kTfRaw) : 0;
+    const TileRec ft = decode_tile<INNER>(P, first_tile);
+    const int npre = first_tile >= 0 ? (ft.kc1 - ft.kc0 < kTfRaw ? ft.kc1 - ft.kc0 : kTfRaw) : 0;
     if (warp == 4 && lane == 0) {
         prefetch_tensormap(&tmap);
-        if (first_tile >= 0) {
-            int64_t ib, ot;
-            tile_coords<INNER>(P, ftb, ib, ot);
-            for (int j = 0; j < npre; ++j) {
-                mbar_arrive_expect_tx(&rfull[j], (uint32_t)kTfBox);
-                tma_load_3d(boxes + j * kTfBox, &tmap, &rfull[j], (fkc0 + j) * 32, (int)(ib * P.I_T),
-                            (int)(ot * P.O_T));
-            }
+        for (int j = 0; j < npre; ++j) {
+            mbar_arrive_expect_tx(&rfull[j], (uint32_t)kTfBox);
+            tma_load_3d(boxes + j * kTfBox, &tmap, &rfull[j], (ft.kc0 + j) * 32, ft.ib * P.I_T, ft.ot * P.O_T);
         }
     }
     pdl_wait();
@@ -882,13 +964,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
                     record_device_error(P.err, kErrWaitFull);
                     break;
                 }
-                const int t = tile_ring[slot];
+                const TileRec tr = tile_ring[slot];
                 mbar_arrive(&sempty[slot]);
-                if (t < 0) break;
-                int64_t tb;
-                int kc0, kc1;
-                tile_chunks(P, t, tb, kc0, kc1);
-                for (int kc = kc0; kc < kc1; ++kc, ++g) {
+                if (tr.t < 0) break;
+                for (int kc = tr.kc0; kc < tr.kc1; ++kc, ++g) {
                     const int bs = (int)(g % kTfB);
                     // slot bs last held chunk g - kTfB: wait for that chunk's MMAs
                     if (g >= kTfB && !mbar_wait_bounded(&done[(g - kTfB) % kTrDone],
@@ -924,13 +1003,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
                     const unsigned int grab = atomicAdd(P.sched, 1u) + (unsigned int)gridDim.x;
                     t = grab < (unsigned int)P.n_tiles ? (int)grab : -1;
                 }
-                tile_ring[slot] = t;
+                const TileRec tr = s == 0 ? ft : decode_tile<INNER>(P, t);
+                tile_ring[slot] = tr;
                 mbar_arrive(&sfull[slot]);
                 if (t < 0) break;
-                int64_t ib, ot, tb;
-                int kc0, kc1;
-                tile_chunks(P, t, tb, kc0, kc1);
-                tile_coords<INNER>(P, tb, ib, ot);
+                const int kc0 = tr.kc0, kc1 = tr.kc1;
                 for (int kc = kc0; kc < kc1; ++kc, ++g) {
                     if (!(s == 0 && kc - kc0 < npre)) {
                         const int rs = (int)(g % kTfRaw);
@@ -940,8 +1017,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
                             break;
                         }
                         mbar_arrive_expect_tx(&rfull[rs], (uint32_t)kTfBox);
-                        tma_load_3d(boxes + rs * kTfBox, &tmap, &rfull[rs], kc * 32, (int)(ib * P.I_T),
-                                    (int)(ot * P.O_T));
+                        tma_load_3d(boxes + rs * kTfBox, &tmap, &rfull[rs], kc * 32, tr.ib * P.I_T, tr.ot * P.O_T);
                         raw_issued = g + 1;
                     }
                 }
@@ -968,14 +1044,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
                 if (lane == 0) record_device_error(P.err, kErrWaitFull);
                 break;
             }
-            const int t = tile_ring[slot];
+            const TileRec tr = tile_ring[slot];
             __syncwarp();
             if (lane == 0) mbar_arrive(&sempty[slot]);
-            if (t < 0) break;
-            int64_t tb;
-            int kc0, kc1;
-            tile_chunks(P, t, tb, kc0, kc1);
-            for (int kc = kc0; kc < kc1; ++kc, ++g) {
+            if (tr.t < 0) break;
+            for (int kc = tr.kc0; kc < tr.kc1; ++kc, ++g) {
                 if ((int)(g % kTfConvGroups) != cg) continue;
                 const int rs = (int)(g % kTfRaw);
                 if (!warp_wait(&rfull[rs], (uint32_t)((g / kTfRaw) & 1))) {
@@ -1069,14 +1142,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
                 if (lane == 0) record_device_error(P.err, kErrWaitFull);
                 break;
             }
-            const int t = tile_ring[slot];
+            const TileRec tr = tile_ring[slot];
             __syncwarp();
             if (lane == 0) mbar_arrive(&sempty[slot]);
-            if (t < 0) break;
-            int64_t tb;
-            int kc0, kc1;
-            tile_chunks(P, t, tb, kc0, kc1);
-            for (int kc = kc0; kc < kc1 && ok; ++kc, ++g) {
+            if (tr.t < 0) break;
+            for (int kc = tr.kc0; kc < tr.kc1 && ok; ++kc, ++g) {
                 if ((int)((g >> 1) & 1) != mg) continue;
                 if ((g & 1) == 0) {
                     pending = true;
@@ -1103,6 +1173,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
     const float* Wt = P.cur ? P.Wb[__ldcg(P.cur + P.w_sel) ^ P.w_flip] : P.W;
     const float* Fit = P.cur ? P.Fib[__ldcg(P.cur + P.fi_sel) ^ P.fi_flip] : P.Fi;
     const int m = threadIdx.x;                       // tile row = TMEM lane
+    const int m_o = m / P.I_T, m_i = m - m_o * P.I_T;   // inner mode: row m = (outer m_o, inner m_i)
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
     int64_t gq = 0;
@@ -1113,28 +1184,14 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
             if (lane == 0) record_device_error(P.err, kErrWaitFull);
             break;
         }
-        const int t = tile_ring[slot];
+        const TileRec tr = tile_ring[slot];
         __syncwarp();
         if (lane == 0) mbar_arrive(&sempty[slot]);
-        if (t < 0) break;
-        int64_t ib, ot, tb;
-        int kc0, kc1;
-        tile_chunks(P, t, tb, kc0, kc1);
-        tile_coords<INNER>(P, tb, ib, ot);
-        bool row_live;
-        const float* wsrc;
-        if (INNER) {
-            const int64_t o = ot * P.O_T + m / P.I_T;
-            row_live = o < P.n_o && ib * P.I_T + m % P.I_T < P.Ii;
-            wsrc = Wt + (row_live ? o : 0) * P.ldw;
-        } else {
-            const int64_t i = ib * 128 + m;
-            row_live = i < P.Ii;
-            wsrc = Fit + (row_live ? i : 0) * P.ldw;
-        }
+        if (tr.t < 0) break;
+        const int kc0 = tr.kc0, kc1 = tr.kc1;
+        // this row's weights, fetched while the tile is being contracted
         float w[RPH];
-#pragma unroll
-        for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(wsrc + p) : 0.f;
+        tile_weights<RPH, INNER>(P, tr, m, m_o, m_i, Wt, Fit, w);
         float y[RPH];
 #pragma unroll
         for (int p = 0; p < RPH; ++p) y[p] = 0.f;
@@ -1152,48 +1209,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
                 if (lane == 0) mbar_arrive(&tempty[d]);
             }
         }
-        if (INNER) {
-            float z[RPH];
+        float z[RPH];
 #pragma unroll
-            for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
-            for (int off = 16; off >= P.I_T; off >>= 1)
-#pragma unroll
-                for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
-            if (lane < P.I_T) {
-#pragma unroll
-                for (int p = 0; p < RPH; ++p) red[(warp * 32 + lane) * RPH + p] = z[p];
-            }
-            named_bar_sync(1, 128);
-            if (ok) {
-                for (int idx = m; idx < P.I_T * P.r; idx += 128) {
-                    const int b = idx / P.r, p = idx - b * P.r;
-                    const float sacc = (red[(0 * 32 + b) * RPH + p] + red[(1 * 32 + b) * RPH + p]) +
-                                       (red[(2 * 32 + b) * RPH + p] + red[(3 * 32 + b) * RPH + p]);
-                    P.part[((int64_t)t * P.I_T + b) * P.RP + p] = sacc;
-                }
-            }
-            named_bar_sync(1, 128);
-        } else {
-            float z[RPH];
-#pragma unroll
-            for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-                for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
-            float mine = 0.f;
-#pragma unroll
-            for (int p = 0; p < RPH; ++p)
-                if (p == lane) mine = z[p];
-            float* zs = zsum + parity * 128;
-            zs[warp * 32 + lane] = mine;
-            named_bar_sync(1, 128);
-            if (warp == 0 && lane < P.r && ok) {
-                const float s4 = (zs[lane] + zs[32 + lane]) + (zs[64 + lane] + zs[96 + lane]);
-                P.part[(int64_t)t * P.RP + lane] = s4;
-            }
-            parity ^= 1;
-        }
+        for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
+        tile_flush<RPH, INNER, true>(P, z, tr.t, ok, warp, lane, m, red, zsum, parity);
     }
     tc_fence_before();
     named_bar_sync(2, 128 + 32 * kTrMmaWarps);
@@ -1485,11 +1504,11 @@ cudaError_t launch_tc_impl(int kind, dim3 grid, size_t smem, cudaStream_t st, co
 
 }  // namespace
 
+int tc_rows_ctas_per_sm() { return kRowCtasPerSm; }
 size_t tc_rows_smem(int rph) {
     const int N = 2 * rph;
-    return (size_t)kTcStages * (kBoxBytes + N * 128) + 1024 + 256 + 2 * 4 * 32 * 4 + 128 * rph * 4;
+    return (size_t)kRowStages * (kBoxBytes + N * 128) + 1024 + kRowMiscBytes + 2 * 4 * 32 * 4 + 128 * rph * 4;
 }
-// (barrier block: 4 full + 4 empty + kDbuf tfull + kDbuf tempty + drain + TMEM slot < 256 bytes)
 size_t tc_last_smem(int rph) {
     const int N = 2 * rph;
     return (size_t)kTcStages * (2 * kBoxBytes + 2 * N * 128) + 1024 + 256;

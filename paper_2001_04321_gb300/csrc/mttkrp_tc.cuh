@@ -39,6 +39,7 @@ struct TcParams {
 };
 
 size_t tc_rows_smem(int rph);
+int tc_rows_ctas_per_sm();          // CTAs of the bf16 rows kernel that share an SM's tensor memory
 size_t tc_last_smem(int rph);
 size_t tc_last_b_bytes(int rph);
 size_t tf32_rows_smem(int rph);
