@@ -195,61 +195,19 @@ __device__ __forceinline__ TileRec decode_tile(const TcParams& P, int t) {
     return r;
 }
 
-// values a lane holds before xor step LVL (offsets 16, 8, 4, 2, 1) of halving_sum
-__host__ __device__ constexpr int halving_count(int n, int lvl) {
-    return lvl == 0 ? n : (halving_count(n, lvl - 1) % 2 == 0 ? halving_count(n, lvl - 1) / 2 : halving_count(n, lvl - 1));
-}
-
-// Sum of z[0..N) over the 32 lanes by recursive halving: at each xor step a lane keeps the
-// half of its values that its lane bit selects and adds the partner's copy of that half, so
-// each step exchanges half as many values as the one before (27 shuffles for N = 24, against
-// 120 for a butterfly on every value).  Once the held values no longer split evenly the
-// remaining steps add all of them.  Afterwards lane L holds, in z[0..halving_count(N, 5)),
-// the sums of values halving_base<N>(L) + j.  Every sum has a fixed order.
-template <int N, int LVL>
-struct HalvingStep {
-    static __device__ __forceinline__ void run(float (&z)[N], int lane) {
-        constexpr int n = halving_count(N, LVL);
-        constexpr int off = 16 >> LVL;
-        if constexpr (n % 2 == 0) {
-            constexpr int h = n / 2;
-            const bool up = (lane & off) != 0;
-#pragma unroll
-            for (int i = 0; i < h; ++i) {
-                const float send = up ? z[i] : z[h + i];
-                const float keep = up ? z[h + i] : z[i];
-                z[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < n; ++i) z[i] += __shfl_xor_sync(0xffffffffu, z[i], off);
-        }
-        HalvingStep<N, LVL + 1>::run(z, lane);
-    }
-};
-template <int N>
-struct HalvingStep<N, 5> {
-    static __device__ __forceinline__ void run(float (&)[N], int) {}
-};
-
-// first value index held by lane L after HalvingStep<N, 0>::run
-template <int N>
-__device__ __forceinline__ int halving_base(int lane) {
-    int b = 0;
-#pragma unroll
-    for (int lvl = 0; lvl < 5; ++lvl) {
-        const int n = halving_count(N, lvl);
-        if (n % 2 == 0 && (lane & (16 >> lvl))) b += n / 2;
-    }
-    return b;
-}
-// lane bits whose lanes hold copies of the same sums (the steps that added all values)
-template <int N>
-__host__ __device__ constexpr int halving_dup_mask() {
-    int m = 0;
-    for (int lvl = 0; lvl < 5; ++lvl)
-        if (halving_count(N, lvl) % 2 != 0) m |= 16 >> lvl;
-    return m;
+// v = *p if pred, else 0, without a dependency on the loaded value at the load: the value is
+// used only at the end of the tile, so the warp must not wait for it here (a select on the
+// loaded value stalled the epilogue for an L2 round trip at every tile boundary)
+__device__ __forceinline__ float ldg_or_zero(const float* ptr, bool pred) {
+    float v;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.b32 q, %2, 0;\n\t"
+        "mov.b32 %0, 0;\n\t"
+        "@q ld.global.nc.f32 %0, [%1];\n\t}"
+        : "=f"(v)
+        : "l"(ptr), "r"((int)pred));
+    return v;
 }
 
 // The epilogue warps' row weights for one tile (w[p] = 0 for dead rows and p >= r): inner mode
@@ -269,68 +227,68 @@ __device__ __forceinline__ void tile_weights(const TcParams& P, const TileRec& t
         src = Fit + (row_live ? i : 0) * P.ldw;
     }
 #pragma unroll
-    for (int p = 0; p < RPH; ++p) w[p] = (row_live && p < P.r) ? __ldg(src + p) : 0.f;
+    for (int p = 0; p < RPH; ++p) w[p] = ldg_or_zero(src + p, row_live && p < P.r);
 }
 
 // A finished tile's output slot from its weighted row sums z (thread m = tile row m), in a
-// fixed order.  The four epilogue warps call this together (it holds named barrier 1).
-//   inner mode: rows m = a I_T + b share inner row b of block ib, so the slot holds their sum
-//     over the tile's O_T outer indices a: lanes with equal lane % I_T by a butterfly, then
-//     the 4 warps through shared memory (red);
-//   outer modes: the sum over all 128 rows: per warp by a butterfly on every value, or by
-//     recursive halving (HALVING; fewer shuffles and adds, measured faster in the TF32 kernel,
-//     where the epilogue shares its issue slots with eight converter warps, and slower in the
-//     bf16 kernel), then the 4 warps through shared memory (zsum, alternate halves per tile so
-//     that one barrier suffices).
-template <int RPH, bool INNER, bool HALVING>
+// fixed order.  The four epilogue warps call this together (it holds named barrier 1); red is
+// 128 x RPH floats of shared memory.  Every row goes to red first.  Tile row m = a I_T + b:
+//   all 128 rows in one output row (outer modes, and the inner mode when I_T = 1): 4 threads
+//     per column p each sum 32 rows (rows 4 i + q) and combine by two shuffles;
+//   inner mode, I_T > 1: rows with equal b share inner row b of block ib, so the slot holds, per
+//     entry (b, p), the sum over the tile's O_T outer indices a: one thread per entry, rows a in
+//     order, even and odd a in two running sums.
+// (Butterflies across the lanes took 1600 to 2300 cycles at each tile boundary, during which
+// the tensor-core pipeline stalled.)
+template <int RPH, bool INNER>
 __device__ __forceinline__ void tile_flush(const TcParams& P, float (&z)[RPH], int t, bool write, int warp, int lane,
-                                           int m, float* red, float* zsum, int& parity) {
-    if (INNER) {
-        for (int off = 16; off >= P.I_T; off >>= 1)
+                                           int m, float* red) {
+    static_assert(RPH % 4 == 0 && RPH <= 32, "rows of red are float4 groups; columns fit in 4 x 8 threads");
+    named_bar_sync(1, 128);                      // the previous tile's readers are done with red
+    float4* dst = reinterpret_cast<float4*>(red + m * RPH);
 #pragma unroll
-            for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
-        // (I_T <= 32 divides 32: lane b of every warp now holds that warp's rows of b)
-        if (lane < P.I_T) {
-#pragma unroll
-            for (int p = 0; p < RPH; ++p) red[(warp * 32 + lane) * RPH + p] = z[p];
-        }
-        named_bar_sync(1, 128);
-        if (write) {
-            for (int idx = m; idx < P.I_T * P.r; idx += 128) {
-                const int b = idx / P.r, p = idx - b * P.r;
-                const float sacc = (red[(0 * 32 + b) * RPH + p] + red[(1 * 32 + b) * RPH + p]) +
-                                   (red[(2 * 32 + b) * RPH + p] + red[(3 * 32 + b) * RPH + p]);
-                P.part[((int64_t)t * P.I_T + b) * P.RP + p] = sacc;
+    for (int j = 0; j < RPH / 4; ++j) dst[j] = make_float4(z[4 * j], z[4 * j + 1], z[4 * j + 2], z[4 * j + 3]);
+    named_bar_sync(1, 128);
+    if (INNER && P.I_T > 1) {
+        if (!write) return;
+        // entries idx = b r + p for idx = m, m + 128, ...: (b, p) stepped without divisions
+        const int IT = P.I_T, OT = 128 / P.I_T;      // O_T I_T = 128, O_T even
+        const int n = IT * P.r;
+        const int db = 128 / P.r, dp = 128 - db * P.r;
+        int b = m / P.r, p = m - b * P.r;
+        for (int idx = m; idx < n; idx += 128) {
+            float s0 = 0.f, s1 = 0.f;
+            const float* col = red + b * RPH + p;
+            for (int a = 0; a < OT; a += 2) {
+                s0 += col[(a * IT) * RPH];
+                s1 += col[((a + 1) * IT) * RPH];
+            }
+            P.part[((int64_t)t * IT + b) * P.RP + p] = s0 + s1;
+            b += db;
+            p += dp;
+            if (p >= P.r) {
+                p -= P.r;
+                ++b;
             }
         }
-        named_bar_sync(1, 128);
     } else {
-        float* zs = zsum + parity * 128;
-        if (HALVING) {
-            HalvingStep<RPH, 0>::run(z, lane);
-            if ((lane & halving_dup_mask<RPH>()) == 0) {
-                const int b0 = halving_base<RPH>(lane);
-#pragma unroll
-                for (int j = 0; j < halving_count(RPH, 5); ++j) zs[warp * 32 + b0 + j] = z[j];
+        // column p = 8 warp + lane % 8, quarter q = lane / 8: rows 4 i + q, two running sums;
+        // the slot index t I_T + 0 = t also holds for the inner mode with I_T = 1
+        const int q = lane >> 3, p = warp * 8 + (lane & 7);
+        float s0 = 0.f, s1 = 0.f;
+        if (p < P.r) {
+#pragma unroll 8
+            for (int i = 0; i < 32; i += 2) {
+                s0 += red[(4 * i + q) * RPH + p];
+                s1 += red[(4 * i + 4 + q) * RPH + p];
             }
-        } else {
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-                for (int p = 0; p < RPH; ++p) z[p] += __shfl_xor_sync(0xffffffffu, z[p], off);
-            float mine = 0.f;
-#pragma unroll
-            for (int p = 0; p < RPH; ++p)
-                if (p == lane) mine = z[p];
-            zs[warp * 32 + lane] = mine;
         }
-        named_bar_sync(1, 128);
-        if (warp == 0 && lane < P.r && write)
-            P.part[(int64_t)t * P.RP + lane] = (zs[lane] + zs[32 + lane]) + (zs[64 + lane] + zs[96 + lane]);
-        parity ^= 1;
+        float sum = s0 + s1;
+        sum += __shfl_xor_sync(0xffffffffu, sum, 8);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 16);
+        if (q == 0 && p < P.r && write) P.part[(int64_t)t * P.RP + p] = sum;
     }
 }
-
 
 template <int RPH, bool INNER>
 __global__ void __launch_bounds__(kTcThreads, kRowCtasPerSm) k_tc_rows(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
@@ -351,8 +309,7 @@ __global__ void __launch_bounds__(kTcThreads, kRowCtasPerSm) k_tc_rows(const __g
     uint64_t* sempty = sfull + kTileRing;       // [kTileRing]: tile index read by all consumers
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + kTileRing);
     TileRec* tile_ring = reinterpret_cast<TileRec*>(base_ptr + kRowStages * kStage + kRowBarBytes);   // [kTileRing]
-    float* zsum = reinterpret_cast<float*>(base_ptr + kRowStages * kStage + kRowMiscBytes);   // [2][4][32]
-    float* red = zsum + 2 * 4 * 32;                                                  // [128][RPH]
+    float* red = reinterpret_cast<float*>(base_ptr + kRowStages * kStage + kRowMiscBytes);   // [128][RPH]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -505,7 +462,6 @@ __global__ void __launch_bounds__(kTcThreads, kRowCtasPerSm) k_tc_rows(const __g
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
     int64_t gq = 0;
-    int parity = 0;
     for (int64_t s = 0; ok; ++s) {
         const int slot = (int)(s % kTileRing);
         if (!warp_wait(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
@@ -544,7 +500,7 @@ __global__ void __launch_bounds__(kTcThreads, kRowCtasPerSm) k_tc_rows(const __g
         float z[RPH];
 #pragma unroll
         for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
-        tile_flush<RPH, INNER, false>(P, z, tr.t, ok, warp, lane, m, red, zsum, parity);
+        tile_flush<RPH, INNER>(P, z, tr.t, ok, warp, lane, m, red);
     }
     tc_fence_before();
     named_bar_sync(2, 160);
@@ -912,8 +868,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
     uint64_t* sempty = sfull + kTileRing;                          // [kTileRing]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + kTileRing);
     TileRec* tile_ring = reinterpret_cast<TileRec*>(tmem_slot + 1);   // [kTileRing]
-    float* zsum = reinterpret_cast<float*>(misc + kTfBars);        // [2][4][32]
-    float* red = zsum + 2 * 4 * 32;                                // [128][RPH]
+    float* red = reinterpret_cast<float*>(misc + kTfBars);         // [128][RPH]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -1177,7 +1132,6 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
     int64_t gq = 0;
-    int parity = 0;
     for (int64_t s = 0; ok; ++s) {
         const int slot = (int)(s % kTileRing);
         if (!warp_wait(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
@@ -1212,7 +1166,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
         float z[RPH];
 #pragma unroll
         for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
-        tile_flush<RPH, INNER, true>(P, z, tr.t, ok, warp, lane, m, red, zsum, parity);
+        tile_flush<RPH, INNER>(P, z, tr.t, ok, warp, lane, m, red);
     }
     tc_fence_before();
     named_bar_sync(2, 128 + 32 * kTrMmaWarps);
@@ -1507,7 +1461,7 @@ cudaError_t launch_tc_impl(int kind, dim3 grid, size_t smem, cudaStream_t st, co
 int tc_rows_ctas_per_sm() { return kRowCtasPerSm; }
 size_t tc_rows_smem(int rph) {
     const int N = 2 * rph;
-    return (size_t)kRowStages * (kBoxBytes + N * 128) + 1024 + kRowMiscBytes + 2 * 4 * 32 * 4 + 128 * rph * 4;
+    return (size_t)kRowStages * (kBoxBytes + N * 128) + 1024 + kRowMiscBytes + 128 * rph * 4;
 }
 size_t tc_last_smem(int rph) {
     const int N = 2 * rph;
@@ -1517,7 +1471,7 @@ size_t tc_last_smem(int rph) {
 size_t tc_last_b_bytes(int rph) { return (size_t)2 * (2 * rph) * 128; }
 size_t tf32_rows_smem(int rph) {
     const int N = 2 * rph;
-    return (size_t)kTfRaw * kTfBox + (size_t)kTfB * N * 128 + 1024 + kTfBars + 2 * 4 * 32 * 4 + 128 * rph * 4;
+    return (size_t)kTfRaw * kTfBox + (size_t)kTfB * N * 128 + 1024 + kTfBars + 128 * rph * 4;
 }
 
 cudaError_t launch_stream_tf32(int kind, int rph, dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& map,
