@@ -904,7 +904,10 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
             tma_load_3d(boxes + j * kTfBox, &tmap, &rfull[j], (ft.kc0 + j) * 32, ft.ib * P.I_T, ft.ot * P.O_T);
         }
     }
-    pdl_wait();
+    // With P.early only the epilogue warps (Grams, V and the row weights that the kernel before
+    // writes) wait for that kernel; the producers, converters and MMA warps read the tensor, the
+    // packed operand and the tile counter, all written two or more kernels back (see k_tc_rows)
+    if (!P.early || warp < 4) pdl_wait();
     pdl_trigger();
 
     if (warp == kTrBWarp) {

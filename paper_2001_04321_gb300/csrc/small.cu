@@ -485,6 +485,46 @@ cudaError_t launch_permute_split(const TensorView& v, int split, void* dst, int6
     return cudaGetLastError();
 }
 
+// The 3-way tensor with its modes reversed: D(i_2, i_1, i_0) = S(i_0, i_1, i_2), rows of D (the
+// i_0 index) with pitch ld_dst, the padding left as it is.  For each i_1 the I_0 x I_2 plane
+// is transposed through 32 x 32 tiles in shared memory, so both sides are coalesced.
+template <typename E>
+__global__ void k_permute_rev3(const E* __restrict__ S, int64_t I0, int64_t I1, int64_t I2, int64_t ld,
+                               E* __restrict__ D, int64_t ld_dst) {
+    __shared__ E tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;   // i_2, i_0 blocks
+    const int tx = threadIdx.x, ty = threadIdx.y;                                    // 32 x 8 threads
+    for (int64_t i1 = blockIdx.z; i1 < I1; i1 += gridDim.z) {
+        for (int k = ty; k < 32; k += 8) {
+            const int64_t i0 = r0 + k, i2 = c0 + tx;
+            if (i0 < I0 && i2 < I2) tile[k][tx] = S[(i0 * I1 + i1) * ld + i2];
+        }
+        __syncthreads();
+        for (int k = ty; k < 32; k += 8) {
+            const int64_t i2 = c0 + k, i0 = r0 + tx;
+            if (i0 < I0 && i2 < I2) D[(i2 * I1 + i1) * ld_dst + i0] = tile[tx][k];
+        }
+        __syncthreads();
+    }
+}
+
+bool permute_rev3_fits(const TensorView& v) {
+    return v.order == 3 && (v.dims[2] + 31) / 32 <= 2147483647 && (v.dims[0] + 31) / 32 <= 65535;
+}
+
+cudaError_t launch_permute_rev3(const TensorView& v, void* dst, int64_t ld_dst, cudaStream_t st) {
+    const int64_t I0 = v.dims[0], I1 = v.dims[1], I2 = v.dims[2];
+    const dim3 grid((unsigned)((I2 + 31) / 32), (unsigned)((I0 + 31) / 32), (unsigned)(I1 < 65535 ? I1 : 65535));
+    if (v.es == 4)
+        k_permute_rev3<uint32_t><<<grid, dim3(32, 8), 0, st>>>(static_cast<const uint32_t*>(v.data), I0, I1, I2, v.ld,
+                                                              static_cast<uint32_t*>(dst), ld_dst);
+    else
+        k_permute_rev3<uint16_t><<<grid, dim3(32, 8), 0, st>>>(static_cast<const uint16_t*>(v.data), I0, I1, I2, v.ld,
+                                                              static_cast<uint16_t*>(dst), ld_dst);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // y += x elementwise (the slab partials of a streamed MTTKRP, summed in slab order)
 __global__ void k_add(float* __restrict__ y, const float* __restrict__ x, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -49,6 +49,9 @@ cudaError_t launch_add(float* y, const float* x, int64_t n, cudaStream_t st);   
 // last mode of the copy (I_{split-1}) with row pitch ld_dst
 bool permute_split_fits(const TensorView& v, int split);
 cudaError_t launch_permute_split(const TensorView& v, int split, void* dst, int64_t ld_dst, cudaStream_t st);
+// 3-way tensor with its modes reversed, (I_2, I_1, I_0), rows pitched by ld_dst
+bool permute_rev3_fits(const TensorView& v);
+cudaError_t launch_permute_rev3(const TensorView& v, void* dst, int64_t ld_dst, cudaStream_t st);
 cudaError_t launch_norm_sq(const TensorView& v, double* parts, double* out, cudaStream_t st);
 cudaError_t launch_residual_sq(const TensorView& v, int r, const float* W, int RP, const float* Ai, const float* Ac,
                                double* parts, double* out, cudaStream_t st);

@@ -68,9 +68,10 @@ struct Solver {
     bool direct = false;
     bool prepped = false;
     __nv_bfloat16* packRows[2] = {nullptr, nullptr};   // packed A_{N-1} of buffer k (row streams)
-    __nv_bfloat16* packLast = nullptr;                 // packed pairing A_{N-2} (last-mode stream)
-    // second layout of the streamed tensor with the last mode first, (I_2, I_0, I_1): the
-    // last mode's MTTKRP then runs the row-stream kernel (outer mode 0 of that layout)
+    __nv_bfloat16* packLast = nullptr;                 // packed pairing factor of the last-mode stream:
+                                                       // A_{N-2} (last-mode kernel) or A_0 (perm)
+    // second layout of the streamed tensor with its modes reversed, (I_2, I_1, I_0): the last
+    // mode's MTTKRP then runs the row-stream kernel (outer mode 0 of that layout)
     bool perm = false;
     TensorView vperm;
     // 4-way tensor-core path: modes 0 and 1 stream the tensor viewed as (I_0, I_1, I_2 I_3)
@@ -327,10 +328,12 @@ struct Solver {
     // cur[n], its factor row in X[n][cur], beta and V (when not formed by the stream) before
     // its own wait, and the stream reads its packed operand and tile counter without waiting;
     // so epilogue n-1 must write none of these.  The last mode's epilogue writes cur, beta,
-    // F-hat and the rows streams' packed operand (n = 0 excluded); epilogue N-2 writes the
-    // last-mode stream's packed operand (n = N-1 excluded); every other epilogue writes only
-    // its own factor buffers, Gram partials and objective partials.
-    static bool early_stream_ok(int n, int N) { return n >= 1 && n < N - 1; }
+    // F-hat and the rows streams' packed operand (n = 0 excluded).  The packed operand of the
+    // last-mode stream comes from epilogue N-2 for the last-mode kernel (n = N-1 excluded) and
+    // from epilogue 0 on the reversed copy (allowed: two launches back).  Every other epilogue
+    // writes only its own factor buffers, Gram partials and objective partials.  Every tile
+    // counter is reset by the epilogue two launches ahead of its stream.
+    bool early_stream_ok(int n) const { return n >= 1 && (n < N - 1 || (perm && n == N - 1 && N == 3)); }
 
     TcParams direct_stream(int n) const {
         const bool use_her = o.her != 0;
@@ -342,8 +345,8 @@ struct Solver {
             T.FcTb[1] = reinterpret_cast<const unsigned char*>(packRows[1]);
             T.fct_sel = N - 1;
         } else if (perm) {
-            // last mode = outer mode 0 of the (I_2, I_0, I_1) layout: it contracts the I_1 index
-            // with the packed pairing A_1 and weights its I_0 rows by the pairing A_0
+            // last mode = outer mode 0 of the (I_2, I_1, I_0) layout: it contracts the I_0 index
+            // with the packed pairing A_0 and weights its I_1 rows by the pairing A_1
             T.FcTb[0] = T.FcTb[1] = reinterpret_cast<const unsigned char*>(packLast);
             T.fct_sel = 0;
         } else {
@@ -361,15 +364,13 @@ struct Solver {
         T.w_sel = 0;
         T.w_flip = (use_her && n > 0) ? 1 : 0;
         if (perm && n == N - 1) {
-            T.Fib[0] = X[0][0];
-            T.Fib[1] = X[0][1];
-            T.fi_sel = 0;
-            T.fi_flip = use_her ? 1 : 0;
+            T.fi_flip = use_her ? 1 : 0;    // rows I_1: the pairing A_hat_1
         }
         // mode 1's packed operand and buffer index come from the previous iteration's last
-        // epilogue and its tile counter from that epilogue too: its tensor can stream in
-        // while the mode-0 epilogue runs
-        T.early = (n == 1 && early_stream_ok(n, N)) ? 1 : 0;
+        // epilogue, and (on the reversed copy) mode 2's from the mode-0 epilogue; their tile
+        // counters are reset two launches ahead: these tensors can stream in while the epilogue
+        // before them runs
+        T.early = early_stream_ok(n) ? 1 : 0;
         GramJob& J = T.job;
         J.rr = r * r;
         J.order = N;
@@ -423,8 +424,9 @@ struct Solver {
                     ep.packA[1] = ep.packH[1] = packRows[1];
                     ep.pack_rph = plan[0].RPH;
                     ep.pack_tf32 = plan[0].tf32 ? 1 : 0;
-                } else if (n == N - 2) {
-                    // the last-mode stream reads the pairing factor of mode N-2
+                } else if (perm ? n == 0 : n == N - 2) {
+                    // the last-mode stream reads the pairing factor of mode N-2, or of mode 0 on
+                    // the reversed copy
                     if (use_her) ep.packH[0] = ep.packH[1] = packLast;
                     else ep.packA[0] = ep.packA[1] = packLast;
                     ep.pack_rph = plan[N - 1].RPH;
@@ -696,20 +698,23 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     size_t tperm_bytes = 0;
     {
         // The last-mode kernel reads its tiles as 32- or 128-row column blocks and is the slowest
-        // of the three streams; a resident second copy of the tensor with the last mode first
-        // (I_2 x I_0 x I_1, one more numel x bytes of HBM) lets that MTTKRP run the row-stream
-        // kernel instead.  Off with NTF_PERM_LAST=0, or when the copy does not fit.
+        // of the three streams; a resident second copy of the tensor with its modes reversed
+        // (I_2 x I_1 x I_0, one more numel x bytes of HBM) lets that MTTKRP run the row-stream
+        // kernel instead.  Its rows contract I_0 against the pairing A_0 (A_hat_0 with HER),
+        // which the mode-0 epilogue writes two kernels ahead, so this stream too can run
+        // ahead of the epilogue before it (early_stream_ok).  Off with NTF_PERM_LAST=0, or when
+        // the copy does not fit.
         const char* env = std::getenv("NTF_PERM_LAST");
         const bool want = !(env && env[0] == '0');
         const TensorView& v = S->vs;
-        if (S->direct && want && permute_split_fits(v, 2)) {
+        if (S->direct && want && permute_rev3_fits(v)) {
             TensorView vp = v;
             vp.dims[0] = v.dims[2];
-            vp.dims[1] = v.dims[0];
-            vp.dims[2] = v.dims[1];
-            vp.C = v.dims[1];
+            vp.dims[1] = v.dims[1];
+            vp.dims[2] = v.dims[0];
+            vp.C = v.dims[0];
             vp.ld = round_up(vp.C, 16 / v.es);
-            vp.Ii = v.dims[0];
+            vp.Ii = v.dims[1];
             vp.n_o = v.dims[2];
             MttkrpPlan pp;
             tperm_bytes = (size_t)vp.rows() * vp.ld * vp.es;
@@ -718,7 +723,7 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
                 cudaMalloc(&tperm, tperm_bytes) == cudaSuccess) {
                 S->allocs.push_back(tperm);
                 vp.data = tperm;
-                // pp.mode stays 0: the output is mode 0 of the (I_2, I_0, I_1) layout
+                // pp.mode stays 0: the output is mode 0 of the (I_2, I_1, I_0) layout
                 S->vperm = vp;
                 S->plan[2] = pp;
                 S->perm = true;
@@ -783,8 +788,8 @@ static ntf_status create_solver(Solver** out, const ntf_tensor* T, float* const*
     for (int n = 0; n < N; ++n) S->wsm[n] = static_cast<unsigned char*>(S->ws_mt) + off_mode[n];
     if (S->perm) {
         NTF_CUDA_TRY(cudaMemsetAsync(tperm, 0, tperm_bytes, st));
-        cudaError_t e = launch_permute_split(S->vs, 2, tperm, S->vperm.ld, st);
-        if (e != cudaSuccess) return bail(cuda_fail(e, "last-mode-first copy"));
+        cudaError_t e = launch_permute_rev3(S->vs, tperm, S->vperm.ld, st);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "reversed copy"));
         // the outer reduction of a 3-way tensor weights its single outer mode by 1
         std::vector<float> ones((size_t)S->vperm.n_o * S->plan[2].RP, 1.0f);
         NTF_CUDA_TRY(cudaMemcpy(S->wsm[2] + S->plan[2].off_W, ones.data(), sizeof(float) * ones.size(),

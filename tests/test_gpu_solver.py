@@ -400,10 +400,11 @@ def test_her_parameters_outside_the_papers_ranges_are_rejected():
 
 
 @pytest.mark.parametrize("form", ["f32", "bf16"])
-def test_last_mode_first_layout_matches_last_mode_kernel(form, monkeypatch):
+def test_reversed_layout_matches_last_mode_kernel(form, monkeypatch):
     # the 3-way tensor-core path streams the last mode's MTTKRP from a second copy of the
-    # tensor with the last mode first (row-stream kernel); NTF_PERM_LAST=0 keeps the
-    # last-mode kernel.  Both agree with the oracle's factors, and with each other.
+    # tensor with its modes reversed (row-stream kernel, running ahead of the epilogue before
+    # it); NTF_PERM_LAST=0 keeps the last-mode kernel.  Both agree with the oracle's factors,
+    # and with each other.
     import paper_2001_04321_gb300 as ntf
     dims, r, iters = (97, 130, 211), 12, 3
     T, init, buf, d, ld, Fd = _setup(dims, r, 1e-2, 4800)
