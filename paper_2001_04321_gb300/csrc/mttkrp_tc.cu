@@ -210,8 +210,23 @@ __device__ __forceinline__ float ldg_or_zero(const float* ptr, bool pred) {
     return v;
 }
 
+// v = *ptr (four floats, 16-byte aligned) if pred, else 0, likewise without waiting for the value
+__device__ __forceinline__ float4 ldg4_or_zero(const float* ptr, bool pred) {
+    float4 v;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.b32 q, %5, 0;\n\t"
+        "mov.b32 %0, 0;\n\tmov.b32 %1, 0;\n\tmov.b32 %2, 0;\n\tmov.b32 %3, 0;\n\t"
+        "@q ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];\n\t}"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(ptr), "r"((int)pred));
+    return v;
+}
+
 // The epilogue warps' row weights for one tile (w[p] = 0 for dead rows and p >= r): inner mode
-// W(o, :) of the row's outer index, outer modes the row's own weight row.
+// W(o, :) of the row's outer index, outer modes the row's own weight row.  Each thread loads its
+// row; where rows are 16-byte aligned, four columns per load (per-column loads from 128
+// different rows kept the load unit busy for hundreds of cycles at every tile boundary).
 template <int RPH, bool INNER>
 __device__ __forceinline__ void tile_weights(const TcParams& P, const TileRec& tr, int m, int m_o, int m_i,
                                              const float* Wt, const float* Fit, float (&w)[RPH]) {
@@ -226,8 +241,100 @@ __device__ __forceinline__ void tile_weights(const TcParams& P, const TileRec& t
         row_live = i < P.Ii;
         src = Fit + (row_live ? i : 0) * P.ldw;
     }
+    if ((P.ldw & 3) == 0 && (P.r & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
 #pragma unroll
-    for (int p = 0; p < RPH; ++p) w[p] = ldg_or_zero(src + p, row_live && p < P.r);
+        for (int j = 0; j < RPH / 4; ++j) {
+            const float4 v = ldg4_or_zero(src + 4 * j, row_live && 4 * j < P.r);
+            w[4 * j] = v.x;
+            w[4 * j + 1] = v.y;
+            w[4 * j + 2] = v.z;
+            w[4 * j + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < RPH; ++p) w[p] = ldg_or_zero(src + p, row_live && p < P.r);
+    }
+}
+
+// The reducer warp of the 3xTF32 rows kernel.  For each tile, once the four epilogue warps have
+// stored the tile's 128 weighted rows z (thread m = tile row m) in red and arrived on zfull, it
+// forms the tile's output slot from them, then frees red (zfree).  Tile row m = a I_T + b
+// (I_T = 1 in the outer modes): the slot holds, per entry (b, p), the sum over the tile's rows
+// a, in order.  It runs off the tensor-core pipeline's critical path: done by the epilogue warps
+// at the end of each tile (tile_flush), the reduction stalled the MMA warps for about 1300 cycles
+// at every tile boundary.  (The bf16 kernel keeps tile_flush: with two CTAs per SM the other CTA
+// covers its boundaries, and an eighth warp measured slower there.)  Every sum has a fixed order.
+template <int RPH, bool INNER>
+__device__ void tile_reducer(const TcParams& P, const TileRec* tile_ring, uint64_t* sfull, uint64_t* sempty,
+                             uint64_t* zfull, uint64_t* zfree, const int* zok, const float* red, int lane) {
+    const int IT = INNER ? P.I_T : 1;
+    int q = 0;                                       // tiles reduced
+    for (int64_t s = 0;; ++s) {
+        const int slot = (int)(s % kTileRing);
+        if (!warp_wait(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
+            if (lane == 0) record_device_error(P.err, kErrWaitFull);
+            break;
+        }
+        const TileRec tr = tile_ring[slot];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sempty[slot]);
+        if (tr.t < 0) break;
+        if (!warp_wait(zfull, (uint32_t)(q & 1))) {
+            if (lane == 0) record_device_error(P.err, kErrWaitFull);
+            break;
+        }
+        const bool write = zok[0] && zok[1] && zok[2] && zok[3];
+        if (IT == 1) {
+            // all 128 rows in one output row: lane p sums column p, rows in order, 4 running sums
+            const int p = lane;
+            if (p < P.r) {
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 8
+                for (int m = 0; m < 128; m += 4) {
+                    s0 += red[(m + 0) * RPH + p];
+                    s1 += red[(m + 1) * RPH + p];
+                    s2 += red[(m + 2) * RPH + p];
+                    s3 += red[(m + 3) * RPH + p];
+                }
+                if (write) P.part[(int64_t)tr.t * P.RP + p] = (s0 + s1) + (s2 + s3);
+            }
+        } else {
+            // entries (b, p), 32 at a time: rows a I_T + b in order, two running sums
+            const int n = IT * P.r, OT = 128 / IT;   // O_T I_T = 128, O_T even
+            for (int idx = lane; idx < n; idx += 32) {
+                const int b = idx / P.r, p = idx - b * P.r;
+                const float* col = red + b * RPH + p;
+                const int stride = IT * RPH;
+                float s0 = 0.f, s1 = 0.f;
+                for (int a = 0; a < OT; a += 2) {
+                    s0 += col[a * stride];
+                    s1 += col[(a + 1) * stride];
+                }
+                if (write) P.part[((int64_t)tr.t * IT + b) * P.RP + p] = s0 + s1;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(zfree);
+        ++q;
+    }
+}
+
+// The epilogue warps' side of the hand-over: wait until the reducer has read the previous tile's
+// rows (zfree), store this tile's weighted rows z (thread m = tile row m) and arrive on zfull.
+template <int RPH>
+__device__ __forceinline__ void tile_handover(const float (&z)[RPH], float* red, int m, int warp, int lane, int q,
+                                              bool& ok, uint64_t* zfull, uint64_t* zfree, int* zok, int* err) {
+    static_assert(RPH % 4 == 0, "rows of red are float4 groups");
+    if (q > 0 && !warp_wait(zfree, (uint32_t)((q - 1) & 1))) {
+        if (lane == 0) record_device_error(err, kErrWaitEmpty);
+        ok = false;
+    }
+    float4* dst = reinterpret_cast<float4*>(red + m * RPH);
+#pragma unroll
+    for (int j = 0; j < RPH / 4; ++j) dst[j] = make_float4(z[4 * j], z[4 * j + 1], z[4 * j + 2], z[4 * j + 3]);
+    if (lane == 0) zok[warp] = ok ? 1 : 0;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(zfull);
 }
 
 // A finished tile's output slot from its weighted row sums z (thread m = tile row m), in a
@@ -725,7 +832,7 @@ constexpr int kTfA = 4;                // tensor-memory A slots of 64 columns (T
 constexpr int kTfDbuf = 4;             // chunks whose accumulators are in flight
 constexpr int kTfAccCols = 64;         // one 64-column accumulator per chunk
 constexpr int kTfBox = 16384;          // 128 rows x 32 fp32
-constexpr int kTfBars = 512;           // barrier block (50 barriers, TMEM slot, tile ring of 4 records)
+constexpr int kTfBars = 640;           // barrier block (52 barriers, TMEM slot, status words, tile ring of 4 records)
 constexpr uint32_t kTfAcol = kTfAccCols * kTfDbuf;
 constexpr uint32_t kTfCols = 512;
 
@@ -771,7 +878,8 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 // needs the accumulator of chunk g + 4 released (the epilogue reads in order), its A slot
 // written by the converters after chunk g + 4, and its factor chunk loaded, so no waiter sees
 // a phase twice removed.
-constexpr int kTrThreads = 512;
+constexpr int kTrThreads = 544;
+constexpr int kTrReducerWarp = 16;     // tile reducer
 constexpr int kTrMmaWarps = 2;
 constexpr int kTrDone = 8;             // done barriers: lcm of the accumulator / A (4) and factor (8) rings
 constexpr int kTrBWarp = 15;           // factor-chunk producer
@@ -823,9 +931,12 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 // 8) columns of each at a time so that no more than 32 loaded values are live
 template <int RPH>
 __device__ __forceinline__ void add_rows(uint32_t tmem_row, int col0, float (&y)[RPH]) {
+    // (at 32 columns 8 at a time: with the row weights and the sums live, 16 at a time would not
+    // fit the 96 registers that the kernel's 17 warps leave each thread)
+    constexpr int kStep = RPH >= 32 ? 8 : 16;
 #pragma unroll
-    for (int c = 0; c < RPH; c += 16) {
-        if (RPH - c >= 16) {
+    for (int c = 0; c < RPH; c += kStep) {
+        if (kStep == 16 && RPH - c >= 16) {
             float h[16], l[16];
             tmem_ld16(tmem_row + col0 + c, h);
             tmem_ld16(tmem_row + col0 + RPH + c, l);
@@ -866,8 +977,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
     uint64_t* drain = tempty + kTfDbuf;                            // [kTrMmaWarps]
     uint64_t* sfull = drain + kTrMmaWarps;                         // [kTileRing]
     uint64_t* sempty = sfull + kTileRing;                          // [kTileRing]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sempty + kTileRing);
-    TileRec* tile_ring = reinterpret_cast<TileRec*>(tmem_slot + 1);   // [kTileRing]
+    uint64_t* zfull = sempty + kTileRing;                          // a tile's rows handed to the reducer
+    uint64_t* zfree = zfull + 1;                                   // ... and read by it
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(zfree + 1);
+    int* zok = reinterpret_cast<int*>(tmem_slot + 1);              // [4]: epilogue warps' status per tile
+    TileRec* tile_ring = reinterpret_cast<TileRec*>(zok + 4);      // [kTileRing]
     float* red = reinterpret_cast<float*>(misc + kTfBars);         // [128][RPH]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -883,9 +997,11 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
         for (int w = 0; w < kTrMmaWarps; ++w) mbar_init(&drain[w], 1);
         for (int k = 0; k < kTileRing; ++k) {
             mbar_init(&sfull[k], 1);
-            // 4 MMA warps, 4 epilogue warps, the factor producer, the converters
-            mbar_init(&sempty[k], kTrMmaWarps + 5 + 4 * kTfConvGroups);
+            // the MMA warps, the 4 epilogue warps, the factor producer, the converters, the reducer
+            mbar_init(&sempty[k], kTrMmaWarps + 5 + 4 * kTfConvGroups + 1);
         }
+        mbar_init(zfull, 4);
+        mbar_init(zfree, 1);
         fence_mbar_init();
     }
     if (warp == 5) tmem_alloc(tmem_slot, kTfCols);
@@ -907,8 +1023,14 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
     // With P.early only the epilogue warps (Grams, V and the row weights that the kernel before
     // writes) wait for that kernel; the producers, converters and MMA warps read the tensor, the
     // packed operand and the tile counter, all written two or more kernels back (see k_tc_rows)
-    if (!P.early || warp < 4) pdl_wait();
+    if (!P.early || warp < 4 || warp == kTrReducerWarp) pdl_wait();
     pdl_trigger();
+
+    if (warp == kTrReducerWarp) {
+        // ------------------------------ tile reducer ------------------------------
+        tile_reducer<RPH, INNER>(P, tile_ring, sfull, sempty, zfull, zfree, zok, red, lane);
+        return;
+    }
 
     if (warp == kTrBWarp) {
         // --------------------- factor-chunk producer (all tiles alike) ---------------------
@@ -1135,6 +1257,7 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
     const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
     bool ok = true;
     int64_t gq = 0;
+    int q = 0;                                       // tiles handed to the reducer
     for (int64_t s = 0; ok; ++s) {
         const int slot = (int)(s % kTileRing);
         if (!warp_wait(&sfull[slot], (uint32_t)((s / kTileRing) & 1))) {
@@ -1145,14 +1268,12 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
         __syncwarp();
         if (lane == 0) mbar_arrive(&sempty[slot]);
         if (tr.t < 0) break;
-        const int kc0 = tr.kc0, kc1 = tr.kc1;
-        // this row's weights, fetched while the tile is being contracted
         float w[RPH];
         tile_weights<RPH, INNER>(P, tr, m, m_o, m_i, Wt, Fit, w);
         float y[RPH];
 #pragma unroll
         for (int p = 0; p < RPH; ++p) y[p] = 0.f;
-        for (int kc = kc0; kc < kc1; ++kc, ++gq) {
+        for (int kc = tr.kc0; kc < tr.kc1; ++kc, ++gq) {
             const int d = (int)(gq % kTfDbuf);
             if (ok && !warp_wait(&done[gq % kTrDone], (uint32_t)((gq / kTrDone) & 1))) {
                 if (lane == 0) record_device_error(P.err, kErrWaitFull);
@@ -1166,16 +1287,15 @@ __global__ void __launch_bounds__(kTrThreads, 1) k_tf32_rows(const __grid_consta
                 if (lane == 0) mbar_arrive(&tempty[d]);
             }
         }
-        float z[RPH];
 #pragma unroll
-        for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
-        tile_flush<RPH, INNER>(P, z, tr.t, ok, warp, lane, m, red);
+        for (int p = 0; p < RPH; ++p) y[p] *= w[p];
+        tile_handover<RPH>(y, red, m, warp, lane, q, ok, zfull, zfree, zok, P.err);
+        ++q;
     }
     tc_fence_before();
     named_bar_sync(2, 128 + 32 * kTrMmaWarps);
 }
 
-// ----------------------------------------------------------------------------
 // TF32 last-mode kernel: FP32 tensor storage, mode N-1 (step a1 for the FP32 form)
 //
 // M_{N-1}(c, :) = sum_o W(o, :) (*) sum_i T(o, i, c) A_{N-2}(i, :).  A tile is one outer
