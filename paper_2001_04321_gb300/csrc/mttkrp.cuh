@@ -34,6 +34,10 @@ struct MttkrpPlan {
     int64_t nb, n_ot, n_tiles;   // row tiles
     int n_kc;
     int n_cs = 1, kc_per = 0;    // tensor-core row kernels: column segments per row tile, chunks per segment
+    // tensor-core row kernels: scheduled units.  Units below n_whole are whole row tiles (their
+    // other segment slots are written as zeros); the rest are single segments of the row tiles
+    // from n_whole on.  n_units = n_whole + (n_tiles - n_whole) n_cs.
+    int64_t n_whole = 0, n_units = 0;
     int G;               // streaming CTAs along the tile axis
     int n_cb;            // last mode: 64-column blocks
     int Smax;

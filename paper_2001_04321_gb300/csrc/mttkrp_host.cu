@@ -126,6 +126,20 @@ static int tf32_mode() {
     return m;
 }
 
+// Row tiles at the end of the 3xTF32 row streams' schedule that are handed out as two column
+// segments, in quarters of the CTA count (NTF_TAIL_SPLIT, read once per process; 2 by default,
+// 0 = none).  Tiles go to CTAs at run time, so the last ones decide when the stream ends: halving
+// them halves the tail.
+static int tail_split_quarters() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("NTF_TAIL_SPLIT");
+        const int x = e ? std::atoi(e) : 2;
+        v = x >= 0 && x <= 16 ? x : 2;
+    }
+    return v;
+}
+
 // Target of scheduled tiles per CTA below which the tensor-core row streams split row tiles into
 // column segments (NTF_SEG_TILES, read once per process; 2 by default).
 static int seg_tiles_per_cta() {
@@ -196,8 +210,20 @@ ntf_status plan_mttkrp(const TensorView& v, int rank, int mode, MttkrpPlan* p) {
             const int64_t ncs = std::max<int64_t>(1, std::min(want, most));
             P.kc_per = (int)ceil_div(P.n_kc, ncs);
             P.n_cs = (int)ceil_div(P.n_kc, P.kc_per);     // no empty segment
+        } else if (P.tile_slots && P.tf32 && P.n_kc >= 8 && tail_split_quarters() > 0) {
+            // many row tiles: only the last ones go out as two column segments of >= 4 chunks.
+            // (3xTF32 only: a 500^3 rank-20 FP32 stream took 94.4 -> 93.0 us; the bf16 streams'
+            // tiles are half as long, and the two slots per row tile that the epilogue then reads
+            // cost the iteration more than the shorter tail saves.)
+            const int64_t split = std::min<int64_t>(P.n_tiles - cap, cap * tail_split_quarters() / 4);
+            if (split > 0) {
+                P.kc_per = (int)ceil_div(P.n_kc, 2);
+                P.n_cs = 2;
+                P.n_whole = P.n_tiles - split;
+            }
         }
-        P.G = (int)std::min<int64_t>(P.n_tiles * P.n_cs, cap);
+        P.n_units = P.n_whole + (P.n_tiles - P.n_whole) * P.n_cs;
+        P.G = (int)std::min<int64_t>(P.n_units, cap);
     }
     P.Smax = 1;
     if (P.kind == ModeKind::Inner && !P.tile_slots) {
@@ -492,10 +518,11 @@ ntf_status run_mttkrp_stream(const TensorView& v, const MttkrpPlan& P, void* wor
         T.O_T = P.O_T;
         T.nb = P.nb;
         T.n_ot = P.n_ot;
-        T.n_tiles = P.n_tiles * P.n_cs;
+        T.n_tiles = P.tile_slots ? P.n_units : P.n_tiles;
         T.n_kc = P.n_kc;
         T.n_cs = P.n_cs;
         T.kc_per = P.kc_per;
+        T.n_whole = P.n_whole;
         T.sched = P.tile_slots ? reinterpret_cast<unsigned int*>(ws + P.off_sched) : nullptr;
         T.RP = P.RP;
         T.r = P.rank;

@@ -165,24 +165,37 @@ __device__ __forceinline__ void drain_ring(uint64_t* full, int R, int64_t issued
 // its chunks [kc0, kc1), and its row block ib and outer block ot.  (Each warp role decoding
 // the index itself with 64-bit divisions took thousands of cycles at every tile boundary, on
 // the epilogue's critical path.)  Tile counts are below 2^31, so 32-bit arithmetic holds.
-// Scheduled tile t is row tile tb = t / n_cs restricted to its column segment t % n_cs; with
-// one segment (the usual case) that is the whole row tile.  Every scheduled tile has its own
-// output slot, so the segments' partial sums meet only in the fixed-order reduction.  The
-// inner mode numbers row tiles over the outer blocks first (tb = ib n_ot + ot), the outer
-// modes over the row blocks first (tb = ot nb + ib).
+// Row tile tb has n_cs output slots, tb n_cs + cs for its column segments cs.  Scheduled units
+// below n_whole are whole row tiles (tb = t; they write slot tb n_cs and zeros to the zext
+// slots after it); the rest are single segments: unit n_whole + u is segment u % n_cs of row
+// tile n_whole + u / n_cs.  Every slot is written once per launch, and the segments' partial
+// sums meet only in the fixed-order reduction.  The inner mode numbers row tiles over the outer
+// blocks first (tb = ib n_ot + ot), the outer modes over the row blocks first (tb = ot nb + ib).
+// t is the output slot (-1: no more tiles).
 struct TileRec {
-    int t, kc0, kc1, ib, ot;
+    int t, kc0, kc1, ib, ot, zext;
 };
 
 template <bool INNER>
 __device__ __forceinline__ TileRec decode_tile(const TcParams& P, int t) {
-    TileRec r{t, 0, 0, 0, 0};
+    TileRec r{t, 0, 0, 0, 0, 0};
     if (t < 0) return r;
     const unsigned int ncs = P.n_cs > 0 ? (unsigned int)P.n_cs : 1u;
     const int per = P.kc_per > 0 ? P.kc_per : P.n_kc;
-    const unsigned int tb = (unsigned int)t / ncs;
-    r.kc0 = (int)((unsigned int)t - tb * ncs) * per;
-    r.kc1 = r.kc0 + per < P.n_kc ? r.kc0 + per : P.n_kc;
+    unsigned int tb;
+    if ((int64_t)t < P.n_whole) {
+        tb = (unsigned int)t;
+        r.kc1 = P.n_kc;
+        r.t = (int)(tb * ncs);
+        r.zext = (int)ncs - 1;
+    } else {
+        const unsigned int u = (unsigned int)t - (unsigned int)P.n_whole;
+        const unsigned int q = u / ncs, cs = u - q * ncs;
+        tb = (unsigned int)P.n_whole + q;
+        r.kc0 = (int)cs * per;
+        r.kc1 = r.kc0 + per < P.n_kc ? r.kc0 + per : P.n_kc;
+        r.t = (int)(tb * ncs + cs);
+    }
     if (INNER) {
         const unsigned int n_ot = (unsigned int)P.n_ot;
         r.ib = (int)(tb / n_ot);
@@ -296,7 +309,10 @@ __device__ void tile_reducer(const TcParams& P, const TileRec* tile_ring, uint64
                     s2 += red[(m + 2) * RPH + p];
                     s3 += red[(m + 3) * RPH + p];
                 }
-                if (write) P.part[(int64_t)tr.t * P.RP + p] = (s0 + s1) + (s2 + s3);
+                if (write) {
+                    P.part[(int64_t)tr.t * P.RP + p] = (s0 + s1) + (s2 + s3);
+                    for (int k = 1; k <= tr.zext; ++k) P.part[(int64_t)(tr.t + k) * P.RP + p] = 0.f;
+                }
             }
         } else {
             // entries (b, p), 32 at a time: rows a I_T + b in order, two running sums
@@ -310,7 +326,10 @@ __device__ void tile_reducer(const TcParams& P, const TileRec* tile_ring, uint64
                     s0 += col[a * stride];
                     s1 += col[(a + 1) * stride];
                 }
-                if (write) P.part[((int64_t)tr.t * IT + b) * P.RP + p] = s0 + s1;
+                if (write) {
+                    P.part[((int64_t)tr.t * IT + b) * P.RP + p] = s0 + s1;
+                    for (int k = 1; k <= tr.zext; ++k) P.part[((int64_t)(tr.t + k) * IT + b) * P.RP + p] = 0.f;
+                }
             }
         }
         __syncwarp();
@@ -348,8 +367,8 @@ __device__ __forceinline__ void tile_handover(const float (&z)[RPH], float* red,
 // (Butterflies across the lanes took 1600 to 2300 cycles at each tile boundary, during which
 // the tensor-core pipeline stalled.)
 template <int RPH, bool INNER>
-__device__ __forceinline__ void tile_flush(const TcParams& P, float (&z)[RPH], int t, bool write, int warp, int lane,
-                                           int m, float* red) {
+__device__ __forceinline__ void tile_flush(const TcParams& P, float (&z)[RPH], int t, int zext, bool write, int warp,
+                                           int lane, int m, float* red) {
     static_assert(RPH % 4 == 0 && RPH <= 32, "rows of red are float4 groups; columns fit in 4 x 8 threads");
     named_bar_sync(1, 128);                      // the previous tile's readers are done with red
     float4* dst = reinterpret_cast<float4*>(red + m * RPH);
@@ -371,6 +390,7 @@ __device__ __forceinline__ void tile_flush(const TcParams& P, float (&z)[RPH], i
                 s1 += col[((a + 1) * IT) * RPH];
             }
             P.part[((int64_t)t * IT + b) * P.RP + p] = s0 + s1;
+            for (int k = 1; k <= zext; ++k) P.part[((int64_t)(t + k) * IT + b) * P.RP + p] = 0.f;
             b += db;
             p += dp;
             if (p >= P.r) {
@@ -393,7 +413,10 @@ __device__ __forceinline__ void tile_flush(const TcParams& P, float (&z)[RPH], i
         float sum = s0 + s1;
         sum += __shfl_xor_sync(0xffffffffu, sum, 8);
         sum += __shfl_xor_sync(0xffffffffu, sum, 16);
-        if (q == 0 && p < P.r && write) P.part[(int64_t)t * P.RP + p] = sum;
+        if (q == 0 && p < P.r && write) {
+            P.part[(int64_t)t * P.RP + p] = sum;
+            for (int k = 1; k <= zext; ++k) P.part[(int64_t)(t + k) * P.RP + p] = 0.f;
+        }
     }
 }
 
@@ -607,7 +630,7 @@ __global__ void __launch_bounds__(kTcThreads, kRowCtasPerSm) k_tc_rows(const __g
         float z[RPH];
 #pragma unroll
         for (int p = 0; p < RPH; ++p) z[p] = w[p] * y[p];
-        tile_flush<RPH, INNER>(P, z, tr.t, ok, warp, lane, m, red);
+        tile_flush<RPH, INNER>(P, z, tr.t, tr.zext, ok, warp, lane, m, red);
     }
     tc_fence_before();
     named_bar_sync(2, 160);

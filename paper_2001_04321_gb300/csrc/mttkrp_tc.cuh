@@ -10,9 +10,10 @@ namespace ntf {
 struct TcParams {
     int64_t C, Ii, n_o;
     int I_T, O_T;
-    int64_t nb, n_ot, n_tiles;      // n_tiles: scheduled tiles (row tiles x column segments)
+    int64_t nb, n_ot, n_tiles;      // n_tiles: scheduled units (see n_whole)
     int n_kc;
-    int n_cs, kc_per;                // column segments per row tile, chunks per segment
+    int n_cs, kc_per;                // column segments (output slots) per row tile, chunks per segment
+    int64_t n_whole;                 // units below n_whole are whole row tiles, the rest single segments
     int RP, r;
     int Smax;
     int64_t Cpad;
