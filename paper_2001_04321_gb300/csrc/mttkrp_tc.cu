@@ -137,9 +137,9 @@ __device__ __forceinline__ void read_rows(uint32_t tmem_row, int col0, float (&y
 // rows kernel (inner / outer modes)
 //
 // Tiles are handed out at run time: the producer takes the next tile index
-// from a device counter (reset before every launch) and passes it to the MMA
-// warp and the epilogue warps through a small ring guarded by its own pair of
-// mbarriers.  Every tile writes its own output slot, so the result does not
+// from a device counter (reset before every launch), decodes it and passes the
+// record to the other warp roles through a small ring guarded by its own pair
+// of mbarriers.  Every tile writes its own output slot, so the result does not
 // depend on which CTA took which tile, and CTAs that stream faster take more
 // tiles (no tail of slow CTAs).
 // ----------------------------------------------------------------------------
@@ -835,12 +835,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_last(const __grid_constant
 // factor chunk) from a ring of its own.  Shared memory carries each tensor byte twice
 // (the TMA write and the converter's read), and eight boxes are in flight.
 //
-// Warps: 0-3 epilogue (as in k_tc_rows), 4 scheduler + TMA producer, 5 MMA issuer and
-// TMEM owner, 6-13 converters (two groups of four), 14 second MMA issuer, 15 factor-chunk
-// producer.  One CTA per SM; 512 TMEM columns (four 64-column accumulators, then four A
-// slots).
+// Warps of the rows kernel: 0-3 epilogue (as in k_tc_rows, but they hand each tile's
+// weighted rows to the reducer), 4 scheduler + TMA producer, 5 MMA issuer and TMEM owner,
+// 6-13 converters (two groups of four), 14 second MMA issuer, 15 factor-chunk producer, 16
+// tile reducer.  One CTA per SM; 512 TMEM columns (four 64-column accumulators, then four A
+// slots).  The last-mode kernel has the first sixteen.
 // ----------------------------------------------------------------------------
-constexpr int kTfThreads = 512;
+constexpr int kTfThreads = 512;       // last-mode kernel
 constexpr int kTfConvGroups = 2;       // converter groups of 4 warps (6-9, 10-13), taking chunks in turn
 constexpr int kTfMmaWarp2 = 14;        // second MMA warp (the first is warp 5); the two take chunks in turn
 constexpr int kTfBWarp = 15;           // factor-chunk producer
